@@ -1,0 +1,327 @@
+"""Benchmark: batched parallel-beam CGLS on the 512^2 x 768-angle x 512-bin
+geometry with 64 slices per GPU, 50 iterations per solve (one step = one
+solve of one batch on a memoized operator).
+
+Prints one JSON line: value = projection + back-projection GFLOP/s of the
+mixed-precision (binary16) solve (2 * nnz * S flops per product, 50
+projections + 51 back projections per step), with the FP32 solve, CGLS
+iterations per second, algorithmic HBM GB/s, the mixed-vs-FP32 error, the
+per-launch roofline of the dominant kernel (the sparse product), the
+clocks seen during the timed region, an end-to-end figure through host
+buffers, and the CPU oracle as a baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank solves its own 64 slices (weak scaling;
+no data exchange) and rank 0 prints the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "batch3d_512"
+METRIC = "proj+backproj GFLOP/s, HBM GB/s, CGLS iter/s: mixed vs FP32 at <=1e-3 rel err"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured", d
+    except Exception:
+        return 6800.0, "fallback", {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, nm in enumerate(names):
+                if r[4 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU FP64 oracle
+# --------------------------------------------------------------------------
+
+def _oracle_setup(w):
+    import oracle
+    g = oracle.Geometry(n=w["n"], m=w["m"], nd=w["nd"], cos_sin=w["cos_sin"])
+    a = oracle.siddon_csr(g)
+    at = oracle.transpose(a)
+    return a, at
+
+
+def _oracle_step(a, at, b, iters):
+    import oracle
+    oracle.cgls(lambda X: oracle.project(a, X), lambda Y: oracle.backproject(at, Y), b, iters)
+
+
+def run_reference(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2009_07226_gb300 import inputs
+    w = inputs.make_workload(WORKLOAD, slices=1, with_images=False)
+    a, at = _oracle_setup(w)
+    nnz = a.nnz
+    b = w["sino"].reshape(1, -1)
+    iters = 2                       # bounded sample: 1 slice, 2 iterations per step
+    for _ in range(args.warmup):
+        _oracle_step(a, at, b, iters)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _oracle_step(a, at, b, iters)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    flops = (2 * iters + 1) * 2.0 * nnz * 1
+    gf = flops / dt / 1e9
+    cores = os.cpu_count()
+    sample = f"1 of 64 slices, {iters} CGLS iterations per step (FP64, CSR oracle)"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": gf, "unit": "GFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": w["n"], "angles": w["m"], "bins": w["nd"],
+                   "slices": 1, "iters": iters},
+        "cpu_baseline": {"value": gf, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": gf, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def cpu_baseline(w):
+    """The oracle, as it stands, on this host's cores: one slice, a few
+    iterations (a bounded sample of the same workload)."""
+    a, at = _oracle_setup(w)
+    b = w["sino"][:1].reshape(1, -1)
+    iters = 2
+    _oracle_step(a, at, b, 1)
+    t0 = time.perf_counter()
+    _oracle_step(a, at, b, iters)
+    dt = time.perf_counter() - t0
+    gf = (2 * iters + 1) * 2.0 * a.nnz / dt / 1e9
+    return {"value": gf, "unit": "GFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"1 of 64 slices, {iters} CGLS iterations, FP64 CSR products (OpenMP)"}
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_07226_gb300 import inputs, xct
+
+    w = inputs.make_workload(WORKLOAD, slice_offset=rank * 64, with_images=False)
+    n, m, nd, S, K = w["n"], w["m"], w["nd"], w["slices"], w["iters"]
+    y = torch.tensor(w["sino"], dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    plans = {k: xct.Plan(n, m, nd, k, cos_sin=w["cos_sin"]) for k in ("f16", "f32")}
+    nnz = plans["f16"].stats()["nnz"]
+    flops_step = (2 * K + 1) * 2.0 * nnz * S
+    xs = {k: torch.empty((S, n, n), dtype=torch.float32, device=dev) for k in plans}
+
+    def step(kind, flags=xct.XCT_CGLS_TIMING):
+        xct.xct_cgls(plans[kind].handle, y, xs[kind], S, K, flags, None, stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(kind, steps):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tp = tb = to = 0.0
+        npj = nbp = 0
+        barrier()
+        launches0 = xct.xct_launch_count()
+        ev0.record(stream)
+        for _ in range(steps):
+            step(kind)
+            st = plans[kind].stats()
+            tp += st["t_project_ms"]
+            tb += st["t_backproject_ms"]
+            to += st["t_other_ms"]
+            npj += st["n_project"]
+            nbp += st["n_backproject"]
+        ev1.record(stream)
+        barrier()
+        launches = xct.xct_launch_count() - launches0
+        ms = ev0.elapsed_time(ev1) / steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, tp / max(npj, 1), tb / max(nbp, 1), to / steps, launches
+
+    for kind in ("f16", "f32"):
+        for _ in range(args.warmup):
+            step(kind)
+    torch.cuda.synchronize()
+
+    peak_hbm, peak_kind, peaks = _peaks()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ms16, proj16, back16, other16, launches = timed("f16", args.steps)
+    ms32, proj32, back32, other32, _ = timed("f32", args.steps)
+    clocks = sampler.stop() if sampler else None
+
+    # graph path (the default call) for reference, untimed by the roofline
+    barrier()
+    g0 = time.perf_counter()
+    for _ in range(max(1, args.steps // 2)):
+        step("f16", 0)
+    torch.cuda.synchronize()
+    graph_ms = (time.perf_counter() - g0) / max(1, args.steps // 2) * 1e3
+
+    # end to end through host buffers (pinned), H2D + solve + D2H every step
+    yh = torch.tensor(w["sino"], dtype=torch.float32).pin_memory()
+    xh = torch.empty((S, n, n), dtype=torch.float32).pin_memory()
+    barrier()
+    e0 = time.perf_counter()
+    e2e_steps = max(1, args.steps // 2)
+    for _ in range(e2e_steps):
+        xct.xct_cgls(plans["f16"].handle, yh, xh, S, K, 0, None, stream)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - e0) / e2e_steps * 1e3
+
+    rel = float(torch.linalg.norm(xs["f16"] - xs["f32"]) / torch.linalg.norm(xs["f32"]))
+
+    if rank != 0:
+        return
+    st16 = plans["f16"].stats()
+    # algorithmic bytes of one product (per slice tile pass): packed entries
+    # (2-byte index + 2-byte value), row pointers, input read, output write
+    rows_a, cols_a = m * nd, n * n
+    alg16 = nnz * 4 + (rows_a + 1) * 8 + S * cols_a * 4 + S * rows_a * 4
+    alg16_bp = nnz * 4 + (cols_a + 1) * 8 + S * rows_a * 4 + S * cols_a * 4
+    achieved = alg16 / (proj16 * 1e-3) / 1e9
+    # shared-memory gather: every entry reads one staged 64-slice vector (128 B)
+    gather = nnz * S * 2
+    smem_peak = 128.0 * 152 * (clocks["sm_mhz"] if clocks and clocks["sm_mhz"] else 1900.0) * 1e6 / 1e9
+    value = flops_step / (ms16 * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms16,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
+        "data": "synthetic (seeded ellipsoid phantom, exact line integrals, Poisson 1e4)",
+        "config": {"workload": WORKLOAD, "n": n, "angles": m, "bins": nd, "slices_per_gpu": S,
+                   "iters": K, "nnz": nnz, "l2": "inputs larger than L2 (packed A 1 GB per product)",
+                   "parallelism": f"slice-sharded x{world}, no collective"},
+        "fp32": {"value": flops_step / (ms32 * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms32,
+                 "cgls_iter_per_s": K / (ms32 * 1e-3)},
+        "cgls_iter_per_s": K / (ms16 * 1e-3),
+        "hbm_gbs_alg": (alg16 * K + alg16_bp * (K + 1)) / (ms16 * 1e-3) / 1e9,
+        "rel_err_mixed_vs_fp32": rel,
+        "graph_ms_per_step": graph_ms,
+        "kernel_ms": {"project_f16": proj16, "backproject_f16": back16, "vector_f16": other16,
+                      "project_f32": proj32, "backproject_f32": back32, "vector_f32": other32},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak_hbm, "unit": "GB/s",
+                     "frac": achieved / peak_hbm, "traffic": None,
+                     "kernel": "spmm_kernel<__half,64> (projection)", "peak_source": peak_kind},
+        "gather_roof": {"achieved_gbs": gather / (proj16 * 1e-3) / 1e9, "peak_gbs": smem_peak,
+                        "frac": gather / (proj16 * 1e-3) / 1e9 / smem_peak},
+        "clocks": clocks,
+        "gpu_launches": launches,
+        "e2e": {"value": flops_step / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+                "h2d_bytes_per_step": int(S * m * nd * 4), "d2h_bytes_per_step": int(S * n * n * 4)},
+        "plan_ms": {"f16": st16["plan_ms"], "f32": plans["f32"].stats()["plan_ms"]},
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * xct.h -- C-ABI of libxct.so: a GB300 (sm_103a) memoized parallel-beam
+ * projector (Siddon system matrix A and its explicit transpose, applied to
+ * batches of slices that share them) and a device-resident CGLS solver.
+ *
+ * Method: "Petascale XCT: 3D Image Reconstruction with Hierarchical
+ * Communications on Multi-GPU Nodes" (SC20).  Section / equation references
+ * below are to that paper.
+ *
+ * Conventions for every entry point:
+ *   - Status codes only: no abort, no exception crosses the ABI.  On an error
+ *     xct_last_error() returns a thread-local message.  Arguments are checked
+ *     before any GPU work is queued.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     that take a stream are stream-ordered and return before the GPU work is
+ *     done, except where stated.
+ *   - Vector arguments (images x, sinograms y) may be device pointers or host
+ *     pointers (pageable or pinned); the library detects which.  Host
+ *     arguments are copied in and out inside the call, which then
+ *     synchronises `stream` before returning.
+ *   - The caller owns every x / y buffer.  A plan owns its matrices; they are
+ *     released by xct_free().
+ *   - Image layout: x[s][iy][ix], S slices of n*n float32, slice-major,
+ *     natural pixel order.  Sinogram layout: y[s][k][j], S slices of
+ *     n_angles*n_det float32.
+ *
+ * Geometry (Sec. II-A, parallel beam; conventions fixed by this library):
+ *   pixel (ix, iy) covers [ix - n/2, ix - n/2 + 1] x [iy - n/2, iy - n/2 + 1];
+ *   ray (k, j) is the line {P : P . (cos th_k, sin th_k) = t_j},
+ *   t_j = (j - (n_det - 1)/2) * det_spacing + det_offset, traversed along
+ *   (-sin th_k, cos th_k).  A[ray, pixel] = length of the ray in the pixel
+ *   (Siddon's method, FP64, segments shorter than min_seg dropped).
+ */
+#ifndef XCT_H
+#define XCT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  XCT_OK = 0,
+  XCT_ERR_INVALID = 1,      /* bad argument or geometry */
+  XCT_ERR_OOM = 2,          /* an allocation failed (nothing leaked) */
+  XCT_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+  XCT_ERR_TIMEOUT = 4,      /* a bounded device wait ran out */
+  XCT_ERR_BREAKDOWN = 5,    /* CGLS: every slice stopped at k = 0 (zero data) */
+  XCT_ERR_UNSUPPORTED = 6   /* valid request outside what this build handles */
+} xct_status;
+
+/* Storage precision of a plan (Sec. III-C).  XCT_F32: values and staged
+ * vectors in float32.  XCT_F16 / XCT_BF16: matrix values stored as
+ * RN16(l * 2^k) (k = 15 for binary16, 0 for bfloat16), input vectors
+ * normalised per slice by 2^-ceil(log2 max|v_s|) and staged in 16 bits,
+ * products accumulated in float32, outputs float32. */
+typedef enum { XCT_F32 = 0, XCT_F16 = 1, XCT_BF16 = 2 } xct_dtype;
+
+typedef struct {
+  int32_t n;              /* grid side (pixels), 1 <= n <= 32768 */
+  int32_t n_angles;       /* M >= 1 */
+  int32_t n_det;          /* N_d >= 1; n_angles * n_det < 2^31 */
+  int32_t hilbert_tile;   /* T of the T x T tiles of Sec. III-A1; 0 -> 8 */
+  const double* cos_sin;  /* host [n_angles][2] (cos, sin) or NULL for
+                             th_k = k*pi/n_angles via the host C library;
+                             copied by xct_plan */
+  double det_spacing;     /* detector bin spacing, finite, != 0 (1.0) */
+  double det_offset;      /* detector offset, finite (0.0) */
+  double min_seg;         /* drop segments shorter than this, >= 0 (1e-9) */
+} xct_geometry;
+
+typedef struct xct_plan_s* xct_plan_t;
+
+/* Plan flags. */
+#define XCT_PLAN_KEEP_F64 1u  /* keep the FP64 CSR of A and A^T on the device
+                                 for xct_plan_export (12 bytes per entry each) */
+
+/*
+ * xct_plan -- build the memoized operator (Sec. II-B memoization; Sec. III-A1
+ * Hilbert ordering; Sec. III-B input buffering; Sec. III-C storage).
+ * Traces every ray on the GPU (count pass, scan, fill pass), orders pixels
+ * and rays along the pseudo-Hilbert curve, forms the explicit transpose
+ * (stable in ray order), and packs both into the staged kernel layout.
+ * Synchronous: returns when the plan is ready (the work runs on `stream`).
+ * `out` receives the plan; on error *out is NULL and nothing is leaked.
+ */
+xct_status xct_plan(const xct_geometry* g, xct_dtype storage, uint32_t flags,
+                    void* stream, xct_plan_t* out);
+
+/* Release a plan and everything it owns (NULL is a no-op).  Synchronises
+ * the device work of the plan first. */
+void xct_free(xct_plan_t plan);
+
+/*
+ * xct_project -- y = A x for S slices sharing A (Sec. II-B: the rays u_{*,j}
+ * trace the same voxels in every slice; Sec. III-B2: fused A X = B).
+ * x: [S][n][n] float32, y: [S][n_angles][n_det] float32 (overwritten).
+ * S = 0 is a no-op.  Arithmetic per the plan's storage precision.
+ */
+xct_status xct_project(xct_plan_t plan, const float* x, float* y, int32_t S,
+                       void* stream);
+
+/*
+ * xct_backproject -- x = A^T y with the stored transpose (Sec. III-B: the
+ * same kernel serves projection and back projection).  y: [S][M][N_d],
+ * x: [S][n][n] (overwritten).  Exact adjoint of xct_project in F32 storage.
+ */
+xct_status xct_backproject(xct_plan_t plan, const float* y, float* x,
+                           int32_t S, void* stream);
+
+/* CGLS flags. */
+#define XCT_CGLS_X0 1u        /* start from the x passed in (else from 0) */
+#define XCT_CGLS_NO_GRAPH 2u  /* launch kernels directly, no CUDA graph */
+#define XCT_CGLS_TIMING 4u    /* time each phase with CUDA events (implies
+                                 NO_GRAPH); read back with xct_plan_stats */
+
+/*
+ * xct_cgls -- least squares min ||y_s - A x_s|| for each slice s (Eq. 1 with
+ * R = 0 and no constraint), `iters` CGLS iterations: one initial back
+ * projection, then one projection and one back projection per iteration
+ * (Table IV footnote: 30 projections, 31 back projections).  Dot products,
+ * norms and the alpha/beta updates run on the GPU in FP64, per slice.
+ * y: [S][M][N_d] float32; x: [S][n][n] float32, in = x0 if XCT_CGLS_X0,
+ * out = solution.  resid: NULL, or host/device double [iters+1][S][2]
+ * receiving (||r_k||, ||A^T r_k||) per iteration and slice.
+ * A slice whose gamma or delta becomes exactly 0 stops silently (its x is
+ * final).  Returns XCT_ERR_BREAKDOWN only if every slice stopped at k = 0;
+ * x then holds x0 (or zeros).  The iteration runs as one CUDA graph unless
+ * flags say otherwise.
+ */
+xct_status xct_cgls(xct_plan_t plan, const float* y, float* x, int32_t S,
+                    int32_t iters, uint32_t flags, double* resid, void* stream);
+
+typedef struct {
+  int64_t n_rays, n_pix, nnz;        /* rows of A, columns of A, entries */
+  int32_t storage;                   /* xct_dtype */
+  int32_t rows_per_block;            /* rows of one thread block */
+  int32_t stage_capacity;            /* pixels (or rays) per staged buffer */
+  int32_t reserved;
+  int64_t stages_a, stages_at;       /* staged buffers over all blocks */
+  int64_t slots_a, slots_at;         /* stored entries incl. padding */
+  int64_t bytes_a, bytes_at;         /* device bytes of each packed form */
+  double plan_ms;                    /* wall time of xct_plan */
+  /* filled by the last xct_cgls run with XCT_CGLS_TIMING: */
+  double t_project_ms, t_backproject_ms, t_other_ms;
+  int64_t n_project, n_backproject;
+} xct_stats;
+
+xct_status xct_plan_stats(xct_plan_t plan, xct_stats* out);
+
+/* What xct_plan_export returns. */
+#define XCT_EXPORT_A_F64 0      /* A as traced (FP64), needs XCT_PLAN_KEEP_F64 */
+#define XCT_EXPORT_AT_F64 1     /* A^T as transposed (FP64), same */
+#define XCT_EXPORT_A_STORED 2   /* A decoded from the packed kernel layout:
+                                   the stored value, de-normalised */
+#define XCT_EXPORT_AT_STORED 3  /* A^T decoded likewise */
+
+/*
+ * xct_plan_export -- copy a matrix to host memory in canonical form: natural
+ * row order, natural column ids ascending inside each row.  rowptr: int64
+ * [rows+1], col: int32 [nnz], val: double [nnz] (all host).  With rowptr ==
+ * NULL only *nnz is written.  Synchronous.  For verification and tooling.
+ */
+xct_status xct_plan_export(xct_plan_t plan, int32_t what, int64_t* rowptr,
+                           int32_t* col, double* val, int64_t* nnz);
+
+/* The pseudo-Hilbert orderings (Sec. III-A1) used by the plan: pix[natural
+ * pixel id] = ordered id (n*n entries), ray[natural ray id] = ordered id
+ * (M*N_d entries); host int32 arrays, either may be NULL.  Synchronous. */
+xct_status xct_plan_order(xct_plan_t plan, int32_t* pix, int32_t* ray);
+
+/*
+ * Device memory.  By default the library allocates with cudaMallocAsync /
+ * cudaFreeAsync on the call's stream.  A caller may route every allocation
+ * through its own allocator (e.g. a framework's caching allocator); the
+ * callbacks must be thread-safe and remain valid until reset.  alloc returns
+ * NULL on failure (the library then returns XCT_ERR_OOM and frees what it
+ * took).  Passing NULL, NULL restores the default.
+ */
+typedef void* (*xct_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*xct_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+xct_status xct_set_allocator(xct_alloc_fn alloc, xct_free_fn release, void* ctx);
+
+/* Thread-local message of the last failing call on this thread. */
+const char* xct_last_error(void);
+
+/* Number of kernels this library has launched in the process so far. */
+int64_t xct_launch_count(void);
+
+/* Library version string. */
+const char* xct_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XCT_H */

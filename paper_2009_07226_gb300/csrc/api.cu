@@ -1,0 +1,524 @@
+// C-ABI entry points of libxct.so (declared in include/xct.h).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "xct_internal.cuh"
+#include "xct_vec.cuh"
+
+namespace xct {
+
+// ---------------------------------------------------------------------------
+// errors, allocation hook, launch count
+// ---------------------------------------------------------------------------
+
+static thread_local char g_err[1024] = "";
+std::atomic<int64_t> g_launches{0};
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+namespace {
+struct AllocHook {
+  xct_alloc_fn alloc = nullptr;
+  xct_free_fn release = nullptr;
+  void* ctx = nullptr;
+};
+std::mutex g_hook_mu;
+AllocHook g_hook;
+
+AllocHook hook() {
+  std::lock_guard<std::mutex> lk(g_hook_mu);
+  return g_hook;
+}
+}  // namespace
+
+void* dalloc(size_t bytes, cudaStream_t s) {
+  AllocHook h = hook();
+  if (h.alloc) {
+    void* p = h.alloc(bytes, (void*)s, h.ctx);
+    if (!p) set_error("allocator callback failed for %zu bytes", bytes);
+    return p;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("cudaMallocAsync(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    return nullptr;
+  }
+  return p;
+}
+
+void dfree(void* p, size_t bytes, cudaStream_t s) {
+  if (!p) return;
+  AllocHook h = hook();
+  if (h.release) {
+    h.release(p, bytes, (void*)s, h.ctx);
+    return;
+  }
+  cudaFreeAsync(p, s);
+}
+
+namespace {
+
+bool is_host_pointer(const void* p) {
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type == cudaMemoryTypeHost || at.type == cudaMemoryTypeUnregistered;
+}
+
+// A vector argument that may live on the host: a device view of it.
+struct DevView {
+  float* dev = nullptr;
+  bool host = false;
+};
+
+xct_status device_view(const float* user, size_t count, bool copy_in, Arena& ar, cudaStream_t s,
+                       DevView& v) {
+  v.host = is_host_pointer(user);
+  if (!v.host) {
+    v.dev = const_cast<float*>(user);
+    return XCT_OK;
+  }
+  XCT_TRY(ar.get(&v.dev, count));
+  if (copy_in && count)
+    XCT_TRY_CUDA(cudaMemcpyAsync(v.dev, user, count * sizeof(float), cudaMemcpyHostToDevice, s));
+  return XCT_OK;
+}
+
+xct_status check_plan(xct_plan_t plan) {
+  if (!plan) {
+    set_error("plan is NULL");
+    return XCT_ERR_INVALID;
+  }
+  return XCT_OK;
+}
+
+// Per-phase CUDA-event timing (XCT_CGLS_TIMING).
+struct PhaseTimer {
+  cudaStream_t s = nullptr;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev;
+  cudaEvent_t cur = nullptr;
+  xct_status begin(int kind) {
+    (void)kind;
+    XCT_TRY_CUDA(cudaEventCreate(&cur));
+    XCT_TRY_CUDA(cudaEventRecord(cur, s));
+    return XCT_OK;
+  }
+  xct_status end(int kind) {
+    cudaEvent_t e;
+    XCT_TRY_CUDA(cudaEventCreate(&e));
+    XCT_TRY_CUDA(cudaEventRecord(e, s));
+    ev.push_back({kind, {cur, e}});
+    cur = nullptr;
+    return XCT_OK;
+  }
+  ~PhaseTimer() {
+    for (auto& x : ev) {
+      cudaEventDestroy(x.second.first);
+      cudaEventDestroy(x.second.second);
+    }
+    if (cur) cudaEventDestroy(cur);
+  }
+};
+
+struct CglsBufs {
+  float *X, *R, *P, *Q, *Sv;
+  double *dpart, *gpart, *rpart, *log;
+  uint32_t* max_x;
+  CglsScalars sc;
+};
+
+xct_status spmm_timed(const SpmmArgs& a, int kind, PhaseTimer* tm, cudaStream_t s) {
+  if (tm) XCT_TRY(tm->begin(kind));
+  XCT_TRY(spmm(a, s));
+  if (tm) XCT_TRY(tm->end(kind));
+  return XCT_OK;
+}
+
+// Enqueue the whole solve on stream s (graph-capturable: no host syncs).
+xct_status enqueue_cgls(Plan& p, const float* yd, float* xd, int S, int st, int ntiles, int iters,
+                        bool x0, CglsBufs& B, cudaStream_t s, PhaseTimer* tm) {
+  const int S_pad = st * ntiles;
+  const int64_t npix = p.npix, nray = p.nray;
+  const int k = p.mat_scale_exp;
+  XCT_TRY_CUDA(cudaMemsetAsync(B.sc.max_r, 0, sizeof(uint32_t) * S_pad, s));
+  XCT_TRY(to_internal(yd, B.R, p.ray_inv, nray, S, st, ntiles, B.sc.max_r, s));
+  if (x0) {
+    XCT_TRY_CUDA(cudaMemsetAsync(B.max_x, 0, sizeof(uint32_t) * S_pad, s));
+    XCT_TRY(to_internal(xd, B.X, p.pix_inv, npix, S, st, ntiles, B.max_x, s));
+    SpmmArgs a{&p.la, B.X, B.Q, st, ntiles, p.storage, k, B.max_x, nullptr};
+    XCT_TRY(spmm_timed(a, 0, tm, s));
+    XCT_TRY_CUDA(cudaMemsetAsync(B.sc.max_r, 0, sizeof(uint32_t) * S_pad, s));
+    XCT_TRY(cgls_residual(B.R, B.Q, nray, st, ntiles, B.sc.max_r, B.rpart, s));
+  } else {
+    XCT_TRY_CUDA(cudaMemsetAsync(B.X, 0, sizeof(float) * npix * S_pad, s));
+    XCT_TRY(cgls_residual(B.R, nullptr, nray, st, ntiles, B.sc.max_r, B.rpart, s));
+  }
+  XCT_TRY_CUDA(cudaMemsetAsync(B.P, 0, sizeof(float) * npix * S_pad, s));
+  {
+    SpmmArgs a{&p.lat, B.R, B.Sv, st, ntiles, p.storage, k, B.sc.max_r, B.gpart};
+    XCT_TRY(spmm_timed(a, 1, tm, s));
+  }
+  XCT_TRY(cgls_init_scalars(B.gpart, p.lat.nblocks, B.rpart, B.sc, B.log, S_pad, s));
+  if (tm) XCT_TRY(tm->begin(2));
+  XCT_TRY(cgls_update_p(B.P, B.Sv, npix, st, ntiles, B.sc, s));
+  if (tm) XCT_TRY(tm->end(2));
+  for (int it = 1; it <= iters; ++it) {
+    SpmmArgs ap{&p.la, B.P, B.Q, st, ntiles, p.storage, k, B.sc.max_p, B.dpart};
+    XCT_TRY(spmm_timed(ap, 0, tm, s));
+    if (tm) XCT_TRY(tm->begin(2));
+    XCT_TRY(cgls_alpha(B.dpart, p.la.nblocks, B.sc, S_pad, s));
+    XCT_TRY(cgls_update_xr(B.X, B.P, npix, B.R, B.Q, nray, st, ntiles, B.sc, B.rpart, s));
+    if (tm) XCT_TRY(tm->end(2));
+    SpmmArgs at{&p.lat, B.R, B.Sv, st, ntiles, p.storage, k, B.sc.max_r, B.gpart};
+    XCT_TRY(spmm_timed(at, 1, tm, s));
+    if (tm) XCT_TRY(tm->begin(2));
+    XCT_TRY(cgls_beta(B.gpart, p.lat.nblocks, B.rpart, B.sc, B.log + (size_t)it * S_pad * 2,
+                      S_pad, s));
+    XCT_TRY(cgls_update_p(B.P, B.Sv, npix, st, ntiles, B.sc, s));
+    if (tm) XCT_TRY(tm->end(2));
+  }
+  XCT_TRY(to_natural(B.X, xd, p.pix_inv, npix, S, st, ntiles, s));
+  return XCT_OK;
+}
+
+struct StreamGuard {
+  cudaStream_t s = nullptr;
+  ~StreamGuard() {
+    if (s) cudaStreamDestroy(s);
+  }
+};
+struct EventGuard {
+  cudaEvent_t e = nullptr;
+  ~EventGuard() {
+    if (e) cudaEventDestroy(e);
+  }
+};
+struct GraphGuard {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t x = nullptr;
+  ~GraphGuard() {
+    if (x) cudaGraphExecDestroy(x);
+    if (g) cudaGraphDestroy(g);
+  }
+};
+
+xct_status cgls_impl(Plan& p, const float* y, float* x, int32_t S, int32_t iters, uint32_t flags,
+                     double* resid, cudaStream_t us) {
+  const int st = pick_slices_per_tile(p.storage, S);
+  const int ntiles = (S + st - 1) / st;
+  const int S_pad = st * ntiles;
+  Arena ar(us);
+  DevView yv, xv;
+  XCT_TRY(device_view(y, (size_t)S * p.nray, true, ar, us, yv));
+  const bool x0 = (flags & XCT_CGLS_X0) != 0;
+  XCT_TRY(device_view(x, (size_t)S * p.npix, x0, ar, us, xv));
+  CglsBufs B{};
+  XCT_TRY(ar.get(&B.X, (size_t)p.npix * S_pad));
+  XCT_TRY(ar.get(&B.P, (size_t)p.npix * S_pad));
+  XCT_TRY(ar.get(&B.Sv, (size_t)p.npix * S_pad));
+  XCT_TRY(ar.get(&B.R, (size_t)p.nray * S_pad));
+  XCT_TRY(ar.get(&B.Q, (size_t)p.nray * S_pad));
+  XCT_TRY(ar.get(&B.dpart, (size_t)S_pad * std::max(p.la.nblocks, 1)));
+  XCT_TRY(ar.get(&B.gpart, (size_t)S_pad * std::max(p.lat.nblocks, 1)));
+  XCT_TRY(ar.get(&B.rpart, (size_t)S_pad * kVecBlocks));
+  XCT_TRY(ar.get(&B.log, (size_t)(iters + 1) * S_pad * 2));
+  XCT_TRY(ar.get(&B.max_x, (size_t)S_pad));
+  XCT_TRY(ar.get(&B.sc.gamma, (size_t)S_pad));
+  XCT_TRY(ar.get(&B.sc.alpha, (size_t)S_pad));
+  XCT_TRY(ar.get(&B.sc.beta, (size_t)S_pad));
+  XCT_TRY(ar.get(&B.sc.active, (size_t)S_pad));
+  XCT_TRY(ar.get(&B.sc.active0, (size_t)S_pad));
+  XCT_TRY(ar.get(&B.sc.max_r, (size_t)S_pad));
+  XCT_TRY(ar.get(&B.sc.max_p, (size_t)S_pad));
+
+  const bool timing = (flags & XCT_CGLS_TIMING) != 0;
+  const bool graph = !(flags & (XCT_CGLS_NO_GRAPH | XCT_CGLS_TIMING));
+  if (graph) {
+    StreamGuard cs;
+    EventGuard e0, e1;
+    GraphGuard gg;
+    XCT_TRY_CUDA(cudaStreamCreateWithFlags(&cs.s, cudaStreamNonBlocking));
+    XCT_TRY_CUDA(cudaEventCreateWithFlags(&e0.e, cudaEventDisableTiming));
+    XCT_TRY_CUDA(cudaEventCreateWithFlags(&e1.e, cudaEventDisableTiming));
+    XCT_TRY_CUDA(cudaEventRecord(e0.e, us));
+    XCT_TRY_CUDA(cudaStreamWaitEvent(cs.s, e0.e, 0));
+    XCT_TRY_CUDA(cudaStreamBeginCapture(cs.s, cudaStreamCaptureModeThreadLocal));
+    xct_status st_enq = enqueue_cgls(p, yv.dev, xv.dev, S, st, ntiles, iters, x0, B, cs.s, nullptr);
+    cudaError_t ec = cudaStreamEndCapture(cs.s, &gg.g);
+    if (st_enq != XCT_OK) return st_enq;
+    if (ec != cudaSuccess) {
+      set_error("graph capture failed: %s", cudaGetErrorString(ec));
+      return XCT_ERR_CUDA;
+    }
+    XCT_TRY_CUDA(cudaGraphInstantiate(&gg.x, gg.g, 0));
+    XCT_TRY_CUDA(cudaGraphLaunch(gg.x, cs.s));
+    XCT_TRY_CUDA(cudaEventRecord(e1.e, cs.s));
+    XCT_TRY_CUDA(cudaStreamWaitEvent(us, e1.e, 0));
+    XCT_TRY_CUDA(cudaStreamSynchronize(cs.s));
+  } else {
+    PhaseTimer tm;
+    tm.s = us;
+    XCT_TRY(enqueue_cgls(p, yv.dev, xv.dev, S, st, ntiles, iters, x0, B, us,
+                         timing ? &tm : nullptr));
+    if (timing) {
+      XCT_TRY_CUDA(cudaStreamSynchronize(us));
+      double t[3] = {0, 0, 0};
+      int64_t n[3] = {0, 0, 0};
+      for (auto& e : tm.ev) {
+        float ms = 0;
+        XCT_TRY_CUDA(cudaEventElapsedTime(&ms, e.second.first, e.second.second));
+        t[e.first] += ms;
+        n[e.first] += 1;
+      }
+      p.stats.t_project_ms = t[0];
+      p.stats.t_backproject_ms = t[1];
+      p.stats.t_other_ms = t[2];
+      p.stats.n_project = n[0];
+      p.stats.n_backproject = n[1];
+    }
+  }
+  if (resid) {
+    const bool rh = is_host_pointer(resid);
+    XCT_TRY_CUDA(cudaMemcpy2DAsync(resid, sizeof(double) * 2 * S, B.log, sizeof(double) * 2 * S_pad,
+                                   sizeof(double) * 2 * S, iters + 1,
+                                   rh ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, us));
+  }
+  if (xv.host)
+    XCT_TRY_CUDA(cudaMemcpyAsync(x, xv.dev, sizeof(float) * S * p.npix, cudaMemcpyDeviceToHost, us));
+  std::vector<int> act0((size_t)S_pad);
+  XCT_TRY_CUDA(cudaMemcpyAsync(act0.data(), B.sc.active0, sizeof(int) * S_pad,
+                               cudaMemcpyDeviceToHost, us));
+  XCT_TRY_CUDA(cudaStreamSynchronize(us));
+  bool any = false;
+  for (int i = 0; i < S; ++i) any = any || act0[i];
+  if (!any) {
+    set_error("CGLS breakdown: every slice has A^T r_0 = 0");
+    return XCT_ERR_BREAKDOWN;
+  }
+  return XCT_OK;
+}
+
+xct_status apply_impl(Plan& p, bool transposed, const float* in, float* out, int32_t S,
+                      cudaStream_t s) {
+  const Layout& L = transposed ? p.lat : p.la;
+  const int32_t* in_inv = transposed ? p.ray_inv : p.pix_inv;
+  const int32_t* out_inv = transposed ? p.pix_inv : p.ray_inv;
+  const int64_t nin = L.ncols, nout = L.nrows;
+  const int st = pick_slices_per_tile(p.storage, S);
+  const int ntiles = (S + st - 1) / st;
+  const int S_pad = st * ntiles;
+  Arena ar(s);
+  DevView iv, ov;
+  XCT_TRY(device_view(in, (size_t)S * nin, true, ar, s, iv));
+  XCT_TRY(device_view(out, (size_t)S * nout, false, ar, s, ov));
+  float *Xi, *Yi;
+  uint32_t* mx;
+  XCT_TRY(ar.get(&Xi, (size_t)nin * S_pad));
+  XCT_TRY(ar.get(&Yi, (size_t)nout * S_pad));
+  XCT_TRY(ar.get(&mx, (size_t)S_pad));
+  XCT_TRY_CUDA(cudaMemsetAsync(mx, 0, sizeof(uint32_t) * S_pad, s));
+  XCT_TRY(to_internal(iv.dev, Xi, in_inv, nin, S, st, ntiles, mx, s));
+  SpmmArgs a{&L, Xi, Yi, st, ntiles, p.storage, p.mat_scale_exp, mx, nullptr};
+  XCT_TRY(spmm(a, s));
+  XCT_TRY(to_natural(Yi, ov.dev, out_inv, nout, S, st, ntiles, s));
+  if (ov.host) {
+    XCT_TRY_CUDA(cudaMemcpyAsync(out, ov.dev, sizeof(float) * S * nout, cudaMemcpyDeviceToHost, s));
+    XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  }
+  return XCT_OK;
+}
+
+bool is_finite_d(double v) { return isfinite(v) != 0; }
+
+}  // namespace
+}  // namespace xct
+
+using namespace xct;
+
+// The opaque handle of the C-ABI is the plan itself.
+struct xct_plan_s : public xct::Plan {};
+
+extern "C" {
+
+xct_status xct_plan(const xct_geometry* g, xct_dtype storage, uint32_t flags, void* stream,
+                    xct_plan_t* out) {
+  if (!out) {
+    set_error("out is NULL");
+    return XCT_ERR_INVALID;
+  }
+  *out = nullptr;
+  if (!g) {
+    set_error("geometry is NULL");
+    return XCT_ERR_INVALID;
+  }
+  if (g->n < 1 || g->n > 32768) {
+    set_error("n = %d outside [1, 32768]", g->n);
+    return XCT_ERR_INVALID;
+  }
+  if (g->n_angles < 1 || g->n_det < 1 || (int64_t)g->n_angles * g->n_det >= (1ll << 31)) {
+    set_error("n_angles = %d, n_det = %d: need >= 1 each and a product < 2^31", g->n_angles,
+              g->n_det);
+    return XCT_ERR_INVALID;
+  }
+  if (g->hilbert_tile < 0 || g->hilbert_tile > 4096) {
+    set_error("hilbert_tile = %d outside [0, 4096]", g->hilbert_tile);
+    return XCT_ERR_INVALID;
+  }
+  if (!is_finite_d(g->det_spacing) || g->det_spacing == 0.0 || !is_finite_d(g->det_offset) ||
+      !is_finite_d(g->min_seg) || g->min_seg < 0.0) {
+    set_error("det_spacing must be finite and nonzero, det_offset finite, min_seg finite >= 0");
+    return XCT_ERR_INVALID;
+  }
+  if (storage != XCT_F32 && storage != XCT_F16 && storage != XCT_BF16) {
+    set_error("storage %d is not XCT_F32, XCT_F16 or XCT_BF16", (int)storage);
+    return XCT_ERR_INVALID;
+  }
+  if (flags & ~XCT_PLAN_KEEP_F64) {
+    set_error("unknown plan flags 0x%x", flags);
+    return XCT_ERR_INVALID;
+  }
+  std::unique_ptr<xct_plan_s> p(new xct_plan_s());
+  p->g = *g;
+  p->g.cos_sin = nullptr;
+  p->storage = storage;
+  p->flags = flags;
+  p->cs.resize((size_t)2 * g->n_angles);
+  for (int k = 0; k < g->n_angles; ++k) {
+    if (g->cos_sin) {
+      p->cs[2 * k] = g->cos_sin[2 * k];
+      p->cs[2 * k + 1] = g->cos_sin[2 * k + 1];
+    } else {
+      const double th = (double)k * M_PI / (double)g->n_angles;
+      p->cs[2 * k] = cos(th);
+      p->cs[2 * k + 1] = sin(th);
+    }
+    if (!is_finite_d(p->cs[2 * k]) || !is_finite_d(p->cs[2 * k + 1])) {
+      set_error("angle table entry %d is not finite", k);
+      return XCT_ERR_INVALID;
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    cudaGetLastError();
+    set_error("no CUDA device");
+    return XCT_ERR_CUDA;
+  }
+  xct_status st = build_plan(*p, s);
+  if (st != XCT_OK) {
+    cudaStreamSynchronize(s);
+    return st;
+  }
+  *out = p.release();
+  return XCT_OK;
+}
+
+void xct_free(xct_plan_t plan) {
+  if (!plan) return;
+  cudaDeviceSynchronize();
+  plan->mem.stream = nullptr;
+  delete plan;
+}
+
+xct_status xct_project(xct_plan_t plan, const float* x, float* y, int32_t S, void* stream) {
+  XCT_TRY(check_plan(plan));
+  if (S < 0 || ((!x || !y) && S > 0)) {
+    set_error("bad arguments (S = %d)", S);
+    return XCT_ERR_INVALID;
+  }
+  if (S == 0) return XCT_OK;
+  return apply_impl(*plan, false, x, y, S, static_cast<cudaStream_t>(stream));
+}
+
+xct_status xct_backproject(xct_plan_t plan, const float* y, float* x, int32_t S, void* stream) {
+  XCT_TRY(check_plan(plan));
+  if (S < 0 || ((!x || !y) && S > 0)) {
+    set_error("bad arguments (S = %d)", S);
+    return XCT_ERR_INVALID;
+  }
+  if (S == 0) return XCT_OK;
+  return apply_impl(*plan, true, y, x, S, static_cast<cudaStream_t>(stream));
+}
+
+xct_status xct_cgls(xct_plan_t plan, const float* y, float* x, int32_t S, int32_t iters,
+                    uint32_t flags, double* resid, void* stream) {
+  XCT_TRY(check_plan(plan));
+  if (S < 0 || iters < 0 || ((!x || !y) && S > 0)) {
+    set_error("bad arguments (S = %d, iters = %d)", S, iters);
+    return XCT_ERR_INVALID;
+  }
+  if (flags & ~(XCT_CGLS_X0 | XCT_CGLS_NO_GRAPH | XCT_CGLS_TIMING)) {
+    set_error("unknown CGLS flags 0x%x", flags);
+    return XCT_ERR_INVALID;
+  }
+  if (S == 0) return XCT_OK;
+  return cgls_impl(*plan, y, x, S, iters, flags, resid, static_cast<cudaStream_t>(stream));
+}
+
+xct_status xct_plan_stats(xct_plan_t plan, xct_stats* out) {
+  XCT_TRY(check_plan(plan));
+  if (!out) {
+    set_error("out is NULL");
+    return XCT_ERR_INVALID;
+  }
+  *out = plan->stats;
+  return XCT_OK;
+}
+
+xct_status xct_plan_export(xct_plan_t plan, int32_t what, int64_t* rowptr, int32_t* col,
+                           double* val, int64_t* nnz) {
+  XCT_TRY(check_plan(plan));
+  if (!nnz || what < 0 || what > 3 || (rowptr && (!col || !val))) {
+    set_error("bad export arguments");
+    return XCT_ERR_INVALID;
+  }
+  XCT_TRY_CUDA(cudaDeviceSynchronize());
+  return export_matrix(*plan, what, rowptr, col, val, nnz);
+}
+
+xct_status xct_plan_order(xct_plan_t plan, int32_t* pix, int32_t* ray) {
+  XCT_TRY(check_plan(plan));
+  XCT_TRY_CUDA(cudaDeviceSynchronize());
+  if (pix)
+    XCT_TRY_CUDA(cudaMemcpy(pix, plan->pix_order, sizeof(int32_t) * plan->npix,
+                            cudaMemcpyDeviceToHost));
+  if (ray)
+    XCT_TRY_CUDA(cudaMemcpy(ray, plan->ray_order, sizeof(int32_t) * plan->nray,
+                            cudaMemcpyDeviceToHost));
+  return XCT_OK;
+}
+
+xct_status xct_set_allocator(xct_alloc_fn alloc, xct_free_fn release, void* ctx) {
+  if ((alloc == nullptr) != (release == nullptr)) {
+    set_error("set both allocator callbacks or neither");
+    return XCT_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lk(g_hook_mu);
+  g_hook.alloc = alloc;
+  g_hook.release = release;
+  g_hook.ctx = ctx;
+  return XCT_OK;
+}
+
+const char* xct_last_error(void) { return g_err; }
+
+int64_t xct_launch_count(void) { return g_launches.load(); }
+
+const char* xct_version(void) { return "xct 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,985 @@
+// Plan construction: the memoized system matrix (paper Sec. II-B).
+//
+//  1. pseudo-Hilbert orderings of pixels and rays (Sec. III-A1);
+//  2. Siddon trace of every ray, count pass + scan + fill pass, FP64 with
+//     every product and sum rounded separately (no FMA contraction), so the
+//     matrix is bit-identical to a plain sequential evaluation (Sec. II-A);
+//  3. the explicit transpose, entries of each column in ascending ray order
+//     (Sec. III-B: A and A^T both read from memory);
+//  4. the staged kernel layout of each (Sec. III-B1 input buffering,
+//     III-B4 multi-stage buffering, III-C2 packed {index, value} entries).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+
+#include "xct_internal.cuh"
+
+namespace xct {
+namespace {
+
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double dsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+
+inline unsigned grid_for(int64_t n, int threads, int64_t cap = 0x7fffffffLL) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (unsigned)b;
+}
+
+// ---------------------------------------------------------------------------
+// 1. pseudo-Hilbert ordering
+// ---------------------------------------------------------------------------
+
+// Position of cell (x, y) on the Hilbert curve of a side x side grid (side a
+// power of two), orientation (0,0),(0,1),(1,1),(1,0) at order 1: at every
+// level the quadrant contributes s*s*((3*rx)^ry); the curve inside a lower
+// quadrant is the parent transposed (left) or anti-transposed (right).
+__device__ int64_t hilbert_pos(int64_t side, int64_t x, int64_t y) {
+  int64_t d = 0;
+  for (int64_t s = side >> 1; s > 0; s >>= 1) {
+    int rx = (x & s) ? 1 : 0;
+    int ry = (y & s) ? 1 : 0;
+    d += s * s * (int64_t)((3 * rx) ^ ry);
+    if (ry == 0) {
+      if (rx == 1) {
+        x = side - 1 - x;
+        y = side - 1 - y;
+      }
+      int64_t t = x;
+      x = y;
+      y = t;
+    }
+  }
+  return d;
+}
+
+__global__ void tile_sizes_kernel(int64_t nx, int64_t ny, int64_t T, int64_t ntx, int64_t nty,
+                                  int64_t side, int64_t* tile_size) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= ntx * nty) return;
+  int64_t tx = i % ntx, ty = i / ntx;
+  int64_t w = min(T, nx - tx * T), h = min(T, ny - ty * T);
+  tile_size[hilbert_pos(side, tx, ty)] = w * h;
+}
+
+__global__ void order_kernel(int64_t nx, int64_t ny, int64_t T, int64_t side,
+                             const int64_t* tile_off, int32_t* order, int32_t* inv) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nx * ny) return;
+  int64_t x = i % nx, y = i / nx;
+  int64_t tx = x / T, ty = y / T;
+  int64_t w = min(T, nx - tx * T);
+  int64_t id = tile_off[hilbert_pos(side, tx, ty)] + (y - ty * T) * w + (x - tx * T);
+  order[i] = (int32_t)id;
+  inv[id] = (int32_t)i;
+}
+
+xct_status make_order(int64_t nx, int64_t ny, int64_t T, int32_t* order, int32_t* inv,
+                      cudaStream_t s) {
+  const int64_t ntx = (nx + T - 1) / T, nty = (ny + T - 1) / T;
+  int64_t side = 1;
+  while (side < std::max(ntx, nty)) side <<= 1;
+  if (side * side > (int64_t)1 << 28) {
+    set_error("Hilbert tile grid %lld x %lld too large: raise hilbert_tile", (long long)ntx,
+              (long long)nty);
+    return XCT_ERR_UNSUPPORTED;
+  }
+  Arena tmp(s);
+  int64_t *tsz, *toff;
+  XCT_TRY(tmp.get(&tsz, side * side));
+  XCT_TRY(tmp.get(&toff, side * side + 1));
+  XCT_TRY_CUDA(cudaMemsetAsync(tsz, 0, sizeof(int64_t) * side * side, s));
+  tile_sizes_kernel<<<grid_for(ntx * nty, 256), 256, 0, s>>>(nx, ny, T, ntx, nty, side, tsz);
+  count_launch();
+  XCT_TRY(exclusive_scan_i64(tsz, toff, side * side, s));
+  order_kernel<<<grid_for(nx * ny, 256), 256, 0, s>>>(nx, ny, T, side, toff, order, inv);
+  count_launch();
+  XCT_TRY_CUDA(cudaGetLastError());
+  return XCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// 2. Siddon trace
+// ---------------------------------------------------------------------------
+
+struct Ray {
+  double px, py, dx, dy, half, amin, amax, min_seg;
+  int n;
+};
+
+// Slab clip; false when the ray misses the (closed) grid square or keeps less
+// than min_seg of it.
+__device__ bool ray_setup(int n, double c, double s, double t, double min_seg, Ray& r) {
+  r.n = n;
+  r.min_seg = min_seg;
+  r.half = dmul(0.5, (double)n);
+  r.px = dmul(t, c);
+  r.py = dmul(t, s);
+  r.dx = -s;
+  r.dy = c;
+  double amin = -INFINITY, amax = INFINITY;
+  if (r.dx != 0.0) {
+    double a0 = ddiv(dsub(-r.half, r.px), r.dx), a1 = ddiv(dsub(r.half, r.px), r.dx);
+    double lo = a0 < a1 ? a0 : a1, hi = a0 < a1 ? a1 : a0;
+    if (lo > amin) amin = lo;
+    if (hi < amax) amax = hi;
+  } else if (!(fabs(r.px) <= r.half)) {
+    return false;
+  }
+  if (r.dy != 0.0) {
+    double a0 = ddiv(dsub(-r.half, r.py), r.dy), a1 = ddiv(dsub(r.half, r.py), r.dy);
+    double lo = a0 < a1 ? a0 : a1, hi = a0 < a1 ? a1 : a0;
+    if (lo > amin) amin = lo;
+    if (hi < amax) amax = hi;
+  } else if (!(fabs(r.py) <= r.half)) {
+    return false;
+  }
+  r.amin = amin;
+  r.amax = amax;
+  return dsub(amax, amin) >= min_seg;
+}
+
+// crossing parameter of interior plane i of an axis (p, d)
+__device__ __forceinline__ double plane_alpha(int i, double half, double p, double d) {
+  return ddiv(dsub(dsub((double)i, half), p), d);
+}
+
+// Crossings of one axis strictly inside (amin, amax), in ascending alpha:
+// planes first..last stepping by step (empty when count == 0).  alpha(i) is
+// monotone in i, so each bound is found by bisection on the exact predicate.
+struct AxisWalk {
+  int i, step, left;
+};
+
+__device__ AxisWalk axis_walk(const Ray& r, double p, double d) {
+  AxisWalk w{0, 1, 0};
+  const int n = r.n;
+  if (d == 0.0 || n < 2) return w;
+  if (d > 0.0) {
+    // first i with alpha(i) > amin  (predicate false..true)
+    int lo = 1, hi = n;  // hi = none
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (plane_alpha(mid, r.half, p, d) > r.amin) hi = mid; else lo = mid + 1;
+    }
+    int first = lo;
+    // last i with alpha(i) < amax (predicate true..false)
+    lo = 0;
+    hi = n - 1;  // lo = none
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (plane_alpha(mid, r.half, p, d) < r.amax) lo = mid; else hi = mid - 1;
+    }
+    int last = lo;
+    if (first <= n - 1 && last >= 1 && first <= last) {
+      w.i = first;
+      w.step = 1;
+      w.left = last - first + 1;
+    }
+  } else {
+    // alpha decreasing in i: ascending alpha walks i downwards
+    // last i with alpha(i) > amin (predicate true..false)
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+      int mid = (lo + hi + 1) >> 1;
+      if (plane_alpha(mid, r.half, p, d) > r.amin) lo = mid; else hi = mid - 1;
+    }
+    int top = lo;
+    // first i with alpha(i) < amax (predicate false..true)
+    lo = 1;
+    hi = n;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (plane_alpha(mid, r.half, p, d) < r.amax) hi = mid; else lo = mid + 1;
+    }
+    int bottom = lo;
+    if (top >= 1 && bottom <= n - 1 && bottom <= top) {
+      w.i = top;
+      w.step = -1;
+      w.left = top - bottom + 1;
+    }
+  }
+  return w;
+}
+
+// Walk the merged crossings; sink(pixel, length) for each kept segment.
+template <class Sink>
+__device__ void trace(const Ray& r, Sink& sink) {
+  AxisWalk wx = axis_walk(r, r.px, r.dx);
+  AxisWalk wy = axis_walk(r, r.py, r.dy);
+  double ax = wx.left ? plane_alpha(wx.i, r.half, r.px, r.dx) : 0.0;
+  double ay = wy.left ? plane_alpha(wy.i, r.half, r.py, r.dy) : 0.0;
+  double cur = r.amin;
+  const int n = r.n;
+  while (true) {
+    double nxt;
+    int which;
+    if (wx.left && (!wy.left || ax <= ay)) {
+      nxt = ax;
+      which = 0;
+    } else if (wy.left) {
+      nxt = ay;
+      which = 1;
+    } else {
+      nxt = r.amax;
+      which = 2;
+    }
+    double len = dsub(nxt, cur);
+    if (len >= r.min_seg) {
+      double mid = dmul(dadd(cur, nxt), 0.5);
+      double x = dadd(r.px, dmul(mid, r.dx));
+      double y = dadd(r.py, dmul(mid, r.dy));
+      int ix = (int)floor(dadd(x, r.half));
+      int iy = (int)floor(dadd(y, r.half));
+      ix = ix < 0 ? 0 : (ix > n - 1 ? n - 1 : ix);
+      iy = iy < 0 ? 0 : (iy > n - 1 ? n - 1 : iy);
+      sink(iy * n + ix, len);
+    }
+    cur = nxt;
+    if (which == 2) break;
+    if (which == 0) {
+      wx.i += wx.step;
+      if (--wx.left) ax = plane_alpha(wx.i, r.half, r.px, r.dx);
+    } else {
+      wy.i += wy.step;
+      if (--wy.left) ay = plane_alpha(wy.i, r.half, r.py, r.dy);
+    }
+  }
+}
+
+struct GeomDev {
+  int n, m, nd;
+  double dspace, doff, min_seg;
+  const double* cs;  // device [m][2]
+};
+
+__device__ __forceinline__ double ray_offset(int j, int nd, double dspace, double doff) {
+  return dadd(dmul(dsub((double)j, dmul(0.5, (double)(nd - 1))), dspace), doff);
+}
+
+__device__ bool setup_row(const GeomDev& g, int32_t natural_ray, Ray& r) {
+  int k = natural_ray / g.nd, j = natural_ray % g.nd;
+  return ray_setup(g.n, g.cs[2 * k], g.cs[2 * k + 1], ray_offset(j, g.nd, g.dspace, g.doff),
+                   g.min_seg, r);
+}
+
+struct CountSink {
+  int c = 0;
+  __device__ void operator()(int, double) { ++c; }
+};
+
+struct FillSink {
+  int32_t* col;
+  double* val;
+  const int32_t* pix_order;
+  int64_t pos;
+  __device__ void operator()(int pix, double len) {
+    col[pos] = pix_order[pix];
+    val[pos] = len;
+    ++pos;
+  }
+};
+
+__global__ void siddon_count_kernel(GeomDev g, const int32_t* ray_inv, int64_t nray, int32_t* cnt) {
+  int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (h >= nray) return;
+  Ray r;
+  CountSink sink;
+  if (setup_row(g, ray_inv[h], r)) trace(r, sink);
+  cnt[h] = sink.c;
+}
+
+__global__ void siddon_fill_kernel(GeomDev g, const int32_t* ray_inv, const int32_t* pix_order,
+                                   int64_t nray, const int64_t* rowptr, int32_t* col, double* val) {
+  int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (h >= nray) return;
+  Ray r;
+  FillSink sink{col, val, pix_order, rowptr[h]};
+  if (setup_row(g, ray_inv[h], r)) trace(r, sink);
+}
+
+// ---------------------------------------------------------------------------
+// 3. transpose
+// ---------------------------------------------------------------------------
+
+__global__ void col_count_kernel(const int32_t* col, int64_t nnz, int32_t* ccount) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&ccount[col[e]], 1);
+}
+
+__global__ void transpose_fill_kernel(const int64_t* rowptr, const int32_t* col, const double* val,
+                                      int64_t nrow, unsigned long long* cursor, int32_t* trow,
+                                      double* tval) {
+  int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+    unsigned long long p = atomicAdd(&cursor[col[e]], 1ull);
+    trow[p] = (int32_t)r;
+    tval[p] = val[e];
+  }
+}
+
+__global__ void max_count_kernel(const int32_t* c, int64_t n, int32_t* out) {
+  int32_t m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, c[i]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+// Sort each column's entries by row (bitonic on (row << 32 | position) keys in
+// shared memory), making the transpose independent of atomic arrival order.
+__global__ void __launch_bounds__(256) column_sort_kernel(const int64_t* colptr, int32_t* trow,
+                                                          double* tval, int pow2) {
+  extern __shared__ unsigned long long sk[];
+  double* sv = reinterpret_cast<double*>(sk + pow2);
+  const int64_t c = blockIdx.x;
+  const int64_t b = colptr[c];
+  const int cnt = (int)(colptr[c + 1] - b);
+  if (cnt <= 1) return;
+  int p2 = 1;
+  while (p2 < cnt) p2 <<= 1;
+  for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+    if (i < cnt) {
+      sk[i] = ((unsigned long long)(uint32_t)trow[b + i] << 32) | (unsigned)i;
+      sv[i] = tval[b + i];
+    } else {
+      sk[i] = ~0ull;
+    }
+  }
+  __syncthreads();
+  for (int k = 2; k <= p2; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+        int l = i ^ j;
+        if (l > i) {
+          unsigned long long a = sk[i], bb = sk[l];
+          bool up = (i & k) == 0;
+          if ((a > bb) == up) {
+            sk[i] = bb;
+            sk[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    unsigned long long key = sk[i];
+    trow[b + i] = (int32_t)(key >> 32);
+    tval[b + i] = sv[key & 0xffffffffu];
+  }
+}
+
+xct_status transpose(const int64_t* rowptr, const int32_t* col, const double* val, int64_t nrow,
+                     int64_t ncol, int64_t nnz, int64_t* colptr, int32_t* trow, double* tval,
+                     cudaStream_t s) {
+  Arena tmp(s);
+  int32_t* ccount;
+  unsigned long long* cursor;
+  int32_t* dmax;
+  XCT_TRY(tmp.get(&ccount, ncol));
+  XCT_TRY(tmp.get(&cursor, ncol));
+  XCT_TRY(tmp.get(&dmax, 1));
+  XCT_TRY_CUDA(cudaMemsetAsync(ccount, 0, sizeof(int32_t) * ncol, s));
+  XCT_TRY_CUDA(cudaMemsetAsync(dmax, 0, sizeof(int32_t), s));
+  if (nnz > 0) {
+    col_count_kernel<<<grid_for(nnz, 256, 152 * 64), 256, 0, s>>>(col, nnz, ccount);
+    count_launch();
+  }
+  XCT_TRY(exclusive_scan_i32(ccount, colptr, ncol, s));
+  XCT_TRY_CUDA(cudaMemcpyAsync(cursor, colptr, sizeof(int64_t) * ncol, cudaMemcpyDeviceToDevice, s));
+  if (nnz > 0) {
+    transpose_fill_kernel<<<grid_for(nrow, 128), 128, 0, s>>>(rowptr, col, val, nrow, cursor, trow, tval);
+    max_count_kernel<<<grid_for(ncol, 256, 1024), 256, 0, s>>>(ccount, ncol, dmax);
+    count_launch(2);
+    int32_t hmax = 0;
+    XCT_TRY_CUDA(cudaMemcpyAsync(&hmax, dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    XCT_TRY_CUDA(cudaStreamSynchronize(s));
+    int p2 = 1;
+    while (p2 < hmax) p2 <<= 1;
+    size_t smem = (size_t)p2 * 16;
+    if (smem > 200 * 1024) {
+      set_error("a column holds %d entries; the transpose sort handles at most 12800", hmax);
+      return XCT_ERR_UNSUPPORTED;
+    }
+    if (smem > 48 * 1024)
+      XCT_TRY_CUDA(cudaFuncSetAttribute(column_sort_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (hmax > 1) {
+      column_sort_kernel<<<(unsigned)ncol, 256, smem, s>>>(colptr, trow, tval, p2);
+      count_launch();
+    }
+  }
+  XCT_TRY_CUDA(cudaGetLastError());
+  return XCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// 4. staged kernel layout
+// ---------------------------------------------------------------------------
+
+constexpr int kWinBits = 1 << 18;          // columns per footprint window
+constexpr int kWinWords = kWinBits / 32;
+constexpr int kFpThreads = 512;
+constexpr int kStageChunk = 256;           // stages counted per pass
+
+__device__ int64_t block_sum64(int64_t v, int64_t* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  int64_t t = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+struct CsrView {
+  const int64_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  int64_t nrows, ncols;
+};
+
+__device__ void block_col_range(const CsrView& m, int64_t e0, int64_t e1, int32_t* lo_hi) {
+  int32_t lo = INT32_MAX, hi = -1;
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    int32_t c = m.col[e];
+    lo = min(lo, c);
+    hi = max(hi, c);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if (threadIdx.x == 0) {
+    lo_hi[0] = INT32_MAX;
+    lo_hi[1] = -1;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&lo_hi[0], lo);
+    atomicMax(&lo_hi[1], hi);
+  }
+  __syncthreads();
+}
+
+// Mark the block's columns of window [w0, w0 + kWinBits) in the bitmap.
+__device__ void mark_window(const CsrView& m, int64_t e0, int64_t e1, int64_t w0, uint32_t* bm) {
+  for (int i = threadIdx.x; i < kWinWords; i += blockDim.x) bm[i] = 0;
+  __syncthreads();
+  for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    int64_t c = m.col[e] - w0;
+    if (c >= 0 && c < kWinBits) atomicOr(&bm[c >> 5], 1u << (c & 31));
+  }
+  __syncthreads();
+}
+
+// footprint size (distinct columns) of each block of rows
+__global__ void __launch_bounds__(kFpThreads) fp_count_kernel(CsrView m, int64_t* fp_size) {
+  extern __shared__ uint32_t bm[];
+  __shared__ int64_t red[kFpThreads / 32];
+  __shared__ int32_t lo_hi[2];
+  const int64_t r0 = (int64_t)blockIdx.x * kRowsPerBlock;
+  const int64_t r1 = min(r0 + kRowsPerBlock, m.nrows);
+  const int64_t e0 = m.rowptr[r0], e1 = m.rowptr[r1];
+  block_col_range(m, e0, e1, lo_hi);
+  int64_t total = 0;
+  if (lo_hi[1] >= 0) {
+    for (int64_t w0 = (lo_hi[0] / kWinBits) * (int64_t)kWinBits; w0 <= lo_hi[1]; w0 += kWinBits) {
+      mark_window(m, e0, e1, w0, bm);
+      int64_t c = 0;
+      for (int i = threadIdx.x; i < kWinWords; i += blockDim.x) c += __popc(bm[i]);
+      total += block_sum64(c, red);
+    }
+  }
+  if (threadIdx.x == 0) fp_size[blockIdx.x] = total;
+}
+
+// footprint lists (ascending column) and each entry's footprint position
+__global__ void __launch_bounds__(kFpThreads) fp_fill_kernel(CsrView m, const int64_t* fp_off,
+                                                              int32_t* pix, int32_t* epos) {
+  extern __shared__ uint32_t bm[];
+  int32_t* pre = reinterpret_cast<int32_t*>(bm + kWinWords);
+  __shared__ int64_t red[kFpThreads / 32];
+  __shared__ int32_t lo_hi[2];
+  __shared__ int32_t wtot[kFpThreads / 32];
+  const int64_t r0 = (int64_t)blockIdx.x * kRowsPerBlock;
+  const int64_t r1 = min(r0 + kRowsPerBlock, m.nrows);
+  const int64_t e0 = m.rowptr[r0], e1 = m.rowptr[r1];
+  block_col_range(m, e0, e1, lo_hi);
+  if (lo_hi[1] < 0) return;
+  int64_t base = 0;
+  constexpr int kWordsPerThread = kWinWords / kFpThreads;
+  for (int64_t w0 = (lo_hi[0] / kWinBits) * (int64_t)kWinBits; w0 <= lo_hi[1]; w0 += kWinBits) {
+    mark_window(m, e0, e1, w0, bm);
+    // exclusive scan of per-word popcounts: thread t owns words
+    // [t*kWordsPerThread, (t+1)*kWordsPerThread)
+    int32_t local = 0;
+    for (int k = 0; k < kWordsPerThread; ++k) local += __popc(bm[threadIdx.x * kWordsPerThread + k]);
+    int32_t inc = local;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (lane == 31) wtot[warp] = inc;
+    __syncthreads();
+    int32_t woff = 0;
+    for (int w = 0; w < warp; ++w) woff += wtot[w];
+    int32_t run = woff + inc - local;
+    for (int k = 0; k < kWordsPerThread; ++k) {
+      int idx = threadIdx.x * kWordsPerThread + k;
+      pre[idx] = run;
+      run += __popc(bm[idx]);
+    }
+    __syncthreads();
+    // footprint list
+    for (int i = threadIdx.x; i < kWinWords; i += blockDim.x) {
+      uint32_t bits = bm[i];
+      int32_t p = pre[i];
+      while (bits) {
+        int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        pix[fp_off[blockIdx.x] + base + p] = (int32_t)(w0 + i * 32 + b);
+        ++p;
+      }
+    }
+    // entry positions
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      int64_t c = m.col[e] - w0;
+      if (c >= 0 && c < kWinBits) {
+        uint32_t word = bm[c >> 5];
+        uint32_t below = (c & 31) ? (word & ((1u << (c & 31)) - 1u)) : 0u;
+        epos[e] = (int32_t)(base + pre[c >> 5] + __popc(below));
+      }
+    }
+    int64_t wcount = 0;
+    for (int w = 0; w < kFpThreads / 32; ++w) wcount += wtot[w];
+    base += wcount;
+    __syncthreads();
+  }
+  (void)red;
+}
+
+__global__ void stage_count_kernel(const int64_t* fp_size, int32_t nblocks, int32_t cap,
+                                   int64_t* nst) {
+  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b < nblocks) nst[b] = (fp_size[b] + cap - 1) / cap;
+}
+
+__global__ void stage_pix_kernel(const int64_t* blk_stage, const int64_t* fp_off, int32_t nblocks,
+                                 int32_t cap, int64_t* stage_pix) {
+  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b > nblocks) return;
+  if (b == nblocks) {
+    stage_pix[blk_stage[nblocks]] = fp_off[nblocks];
+    return;
+  }
+  for (int64_t s = blk_stage[b]; s < blk_stage[b + 1]; ++s)
+    stage_pix[s] = fp_off[b] + (s - blk_stage[b]) * cap;
+}
+
+// per (stage, quad): the 4 row counts and the padded slot count
+__global__ void __launch_bounds__(kRowsPerBlock) seg_count_kernel(CsrView m, const int32_t* epos,
+                                                                  const int64_t* blk_stage,
+                                                                  int32_t cap, Seg* seg,
+                                                                  int64_t* slots) {
+  __shared__ uint16_t cnt[kRowsPerBlock][kStageChunk + 2];  // counts <= capacity
+  const int b = blockIdx.x;
+  const int64_t sb = blk_stage[b], ns = blk_stage[b + 1] - sb;
+  const int64_t row = (int64_t)b * kRowsPerBlock + threadIdx.x;
+  const bool has = row < m.nrows;
+  const int64_t e0 = has ? m.rowptr[row] : 0, e1 = has ? m.rowptr[row + 1] : 0;
+  for (int64_t s0 = 0; s0 < ns; s0 += kStageChunk) {
+    for (int k = 0; k < kStageChunk; ++k) cnt[threadIdx.x][k] = 0;
+    for (int64_t e = e0; e < e1; ++e) {
+      int64_t st = epos[e] / cap - s0;
+      if (st >= 0 && st < kStageChunk) cnt[threadIdx.x][st] = (uint16_t)(cnt[threadIdx.x][st] + 1);
+    }
+    __syncthreads();
+    const int64_t nchunk = min((int64_t)kStageChunk, ns - s0);
+    for (int64_t i = threadIdx.x; i < nchunk * kQuads; i += blockDim.x) {
+      int64_t st = i / kQuads;
+      int q = (int)(i % kQuads);
+      Seg sg;
+      int32_t mx = 0;
+      for (int g = 0; g < 4; ++g) {
+        int32_t c = cnt[q * 4 + g][st];
+        sg.cnt[g] = (uint16_t)c;
+        mx = max(mx, c);
+      }
+      sg.off = 0;
+      int64_t gi = (sb + s0 + st) * kQuads + q;
+      seg[gi] = sg;
+      slots[gi] = (int64_t)((mx + 3) / 4) * 16;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void seg_off_kernel(Seg* seg, const int64_t* off, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) seg[i].off = off[i];
+}
+
+template <int EB>
+__global__ void pad_fill_kernel(void* ent, int64_t nslots, uint32_t zero_slot) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nslots;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (EB == 4)
+      static_cast<uint32_t*>(ent)[i] = zero_slot;
+    else
+      static_cast<unsigned long long*>(ent)[i] = zero_slot;
+  }
+}
+
+template <int KIND>  // 0: f32, 1: f16 (x 2^15), 2: bf16
+__device__ __forceinline__ void pack_entry(void* ent, int64_t slot, uint32_t local, double v) {
+  if (KIND == 0) {
+    unsigned long long w = (unsigned long long)local |
+                           ((unsigned long long)__float_as_uint(__double2float_rn(v)) << 32);
+    static_cast<unsigned long long*>(ent)[slot] = w;
+  } else if (KIND == 1) {
+    unsigned short h = __half_as_ushort(__double2half(dmul(v, 32768.0)));
+    static_cast<uint32_t*>(ent)[slot] = (local & 0xffffu) | ((uint32_t)h << 16);
+  } else {
+    unsigned short h = __bfloat16_as_ushort(__double2bfloat16(v));
+    static_cast<uint32_t*>(ent)[slot] = (local & 0xffffu) | ((uint32_t)h << 16);
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(kRowsPerBlock) fill_entries_kernel(CsrView m, const int32_t* epos,
+                                                                     const int64_t* blk_stage,
+                                                                     int32_t cap, const Seg* seg,
+                                                                     void* ent) {
+  __shared__ uint16_t cnt[kRowsPerBlock][kStageChunk + 2];  // counts <= capacity
+  const int b = blockIdx.x;
+  const int64_t sb = blk_stage[b], ns = blk_stage[b + 1] - sb;
+  const int64_t row = (int64_t)b * kRowsPerBlock + threadIdx.x;
+  if (row >= m.nrows) return;
+  const int q = threadIdx.x / 4, g = threadIdx.x % 4;
+  const int64_t e0 = m.rowptr[row], e1 = m.rowptr[row + 1];
+  for (int64_t s0 = 0; s0 < ns; s0 += kStageChunk) {
+    for (int k = 0; k < kStageChunk; ++k) cnt[threadIdx.x][k] = 0;
+    for (int64_t e = e0; e < e1; ++e) {
+      int32_t p = epos[e];
+      int64_t st = p / cap - s0;
+      if (st < 0 || st >= kStageChunk) continue;
+      int32_t k = cnt[threadIdx.x][st];
+      cnt[threadIdx.x][st] = (uint16_t)(k + 1);
+      int64_t slot = seg[(sb + s0 + st) * kQuads + q].off + (k >> 2) * 16 + g * 4 + (k & 3);
+      pack_entry<KIND>(ent, slot, (uint32_t)(p % cap), m.val[e]);
+    }
+  }
+}
+
+xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_t cap, Layout& L,
+                        Arena& keep, cudaStream_t s) {
+  L.nrows = m.nrows;
+  L.ncols = m.ncols;
+  L.cap = cap;
+  L.ebytes = storage == XCT_F32 ? 8 : 4;
+  L.nblocks = (int32_t)((m.nrows + kRowsPerBlock - 1) / kRowsPerBlock);
+  const int32_t nb = L.nblocks;
+  Arena tmp(s);
+  int64_t *fp_size, *fp_off, *nst;
+  int32_t* epos;
+  XCT_TRY(tmp.get(&fp_size, nb));
+  XCT_TRY(tmp.get(&fp_off, nb + 1));
+  XCT_TRY(tmp.get(&nst, nb));
+  XCT_TRY(tmp.get(&epos, nnz));
+  const size_t bm_smem = (size_t)kWinWords * 4;
+  const size_t fill_smem = (size_t)kWinWords * 8;
+  XCT_TRY_CUDA(cudaFuncSetAttribute(fp_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)bm_smem));
+  XCT_TRY_CUDA(cudaFuncSetAttribute(fp_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)fill_smem));
+  if (nb > 0) {
+    fp_count_kernel<<<nb, kFpThreads, bm_smem, s>>>(m, fp_size);
+    count_launch();
+  }
+  XCT_TRY(exclusive_scan_i64(fp_size, fp_off, nb, s));
+  int64_t total_fp = 0;
+  XCT_TRY_CUDA(cudaMemcpyAsync(&total_fp, fp_off + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  L.footprint = total_fp;
+  Arena own(s);
+  XCT_TRY(own.get(&L.pix, total_fp));
+  XCT_TRY(own.get(&L.blk_stage, nb + 1));
+  if (nb > 0) {
+    fp_fill_kernel<<<nb, kFpThreads, fill_smem, s>>>(m, fp_off, L.pix, epos);
+    stage_count_kernel<<<grid_for(nb, 256), 256, 0, s>>>(fp_size, nb, cap, nst);
+    count_launch(2);
+  }
+  XCT_TRY(exclusive_scan_i64(nst, L.blk_stage, nb, s));
+  XCT_TRY_CUDA(cudaMemcpyAsync(&L.nstages, L.blk_stage + nb, sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, s));
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  XCT_TRY(own.get(&L.stage_pix, L.nstages + 1));
+  XCT_TRY(own.get(&L.seg, L.nstages * kQuads));
+  int64_t *slots, *slot_off;
+  XCT_TRY(tmp.get(&slots, L.nstages * kQuads));
+  XCT_TRY(tmp.get(&slot_off, L.nstages * kQuads + 1));
+  stage_pix_kernel<<<grid_for(nb + 1, 256), 256, 0, s>>>(L.blk_stage, fp_off, nb, cap, L.stage_pix);
+  count_launch();
+  if (nb > 0) {
+    seg_count_kernel<<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, slots);
+    count_launch();
+  }
+  XCT_TRY(exclusive_scan_i64(slots, slot_off, L.nstages * kQuads, s));
+  if (L.nstages > 0) {
+    seg_off_kernel<<<grid_for(L.nstages * kQuads, 256), 256, 0, s>>>(L.seg, slot_off,
+                                                                    L.nstages * kQuads);
+    count_launch();
+  }
+  XCT_TRY_CUDA(cudaMemcpyAsync(&L.nslots, slot_off + L.nstages * kQuads, sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, s));
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  if (L.ebytes == 8) {
+    unsigned long long* e;
+    XCT_TRY(own.get(&e, L.nslots));
+    L.ent = e;
+    pad_fill_kernel<8><<<grid_for(L.nslots, 256, 152 * 32), 256, 0, s>>>(L.ent, L.nslots, (uint32_t)cap);
+  } else {
+    uint32_t* e;
+    XCT_TRY(own.get(&e, L.nslots));
+    L.ent = e;
+    pad_fill_kernel<4><<<grid_for(L.nslots, 256, 152 * 32), 256, 0, s>>>(L.ent, L.nslots, (uint32_t)cap);
+  }
+  count_launch();
+  if (nb > 0) {
+    if (storage == XCT_F32)
+      fill_entries_kernel<0><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent);
+    else if (storage == XCT_F16)
+      fill_entries_kernel<1><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent);
+    else
+      fill_entries_kernel<2><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent);
+    count_launch();
+  }
+  XCT_TRY_CUDA(cudaGetLastError());
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  L.bytes = (int64_t)L.nslots * L.ebytes + L.nstages * (int64_t)sizeof(Seg) +
+            (L.nstages + 1) * 8 + (int64_t)(nb + 1) * 8 + total_fp * 4;
+  own.move_to(keep);
+  return XCT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// orchestration
+// ---------------------------------------------------------------------------
+
+xct_status build_plan(Plan& p, cudaStream_t s) {
+  auto t0 = std::chrono::steady_clock::now();
+  const xct_geometry& g = p.g;
+  p.npix = (int64_t)g.n * g.n;
+  p.nray = (int64_t)g.n_angles * g.n_det;
+  p.mat_scale_exp = p.storage == XCT_F16 ? 15 : 0;
+  const int T = g.hilbert_tile > 0 ? g.hilbert_tile : 8;
+  Arena& keep = p.mem;
+  keep.stream = s;
+  Arena tmp(s);
+
+  double* cs_dev;
+  XCT_TRY(tmp.get(&cs_dev, 2 * (size_t)g.n_angles));
+  XCT_TRY_CUDA(cudaMemcpyAsync(cs_dev, p.cs.data(), sizeof(double) * 2 * g.n_angles,
+                               cudaMemcpyHostToDevice, s));
+  XCT_TRY(keep.get(&p.pix_order, p.npix));
+  XCT_TRY(keep.get(&p.pix_inv, p.npix));
+  XCT_TRY(keep.get(&p.ray_order, p.nray));
+  XCT_TRY(keep.get(&p.ray_inv, p.nray));
+  XCT_TRY(make_order(g.n, g.n, T, p.pix_order, p.pix_inv, s));
+  XCT_TRY(make_order(g.n_det, g.n_angles, T, p.ray_order, p.ray_inv, s));
+
+  GeomDev gd{g.n, g.n_angles, g.n_det, g.det_spacing, g.det_offset, g.min_seg, cs_dev};
+  int32_t* cnt;
+  int64_t* rowptr;
+  XCT_TRY(tmp.get(&cnt, p.nray));
+  Arena f64(s);  // FP64 CSR / CSC, kept only with XCT_PLAN_KEEP_F64
+  XCT_TRY(f64.get(&rowptr, p.nray + 1));
+  siddon_count_kernel<<<grid_for(p.nray, 128), 128, 0, s>>>(gd, p.ray_inv, p.nray, cnt);
+  count_launch();
+  XCT_TRY(exclusive_scan_i32(cnt, rowptr, p.nray, s));
+  XCT_TRY_CUDA(cudaMemcpyAsync(&p.nnz, rowptr + p.nray, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  int32_t* col;
+  double* val;
+  XCT_TRY(f64.get(&col, p.nnz));
+  XCT_TRY(f64.get(&val, p.nnz));
+  siddon_fill_kernel<<<grid_for(p.nray, 128), 128, 0, s>>>(gd, p.ray_inv, p.pix_order, p.nray,
+                                                          rowptr, col, val);
+  count_launch();
+  XCT_TRY_CUDA(cudaGetLastError());
+
+  int64_t* colptr;
+  int32_t* trow;
+  double* tval;
+  XCT_TRY(f64.get(&colptr, p.npix + 1));
+  XCT_TRY(f64.get(&trow, p.nnz));
+  XCT_TRY(f64.get(&tval, p.nnz));
+  XCT_TRY(transpose(rowptr, col, val, p.nray, p.npix, p.nnz, colptr, trow, tval, s));
+
+  const int32_t cap = kDefaultCapacity;
+  CsrView ma{rowptr, col, val, p.nray, p.npix};
+  XCT_TRY(build_layout(ma, p.nnz, p.storage, cap, p.la, keep, s));
+  CsrView mt{colptr, trow, tval, p.npix, p.nray};
+  XCT_TRY(build_layout(mt, p.nnz, p.storage, cap, p.lat, keep, s));
+
+  if (p.flags & XCT_PLAN_KEEP_F64) {
+    p.a_rowptr = rowptr; p.a_col = col; p.a_val = val;
+    p.t_rowptr = colptr; p.t_col = trow; p.t_val = tval;
+    f64.move_to(keep);
+  }
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  tmp.release();
+  f64.release();
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+
+  auto t1 = std::chrono::steady_clock::now();
+  xct_stats& st = p.stats;
+  st.n_rays = p.nray;
+  st.n_pix = p.npix;
+  st.nnz = p.nnz;
+  st.storage = p.storage;
+  st.rows_per_block = kRowsPerBlock;
+  st.stage_capacity = cap;
+  st.stages_a = p.la.nstages;
+  st.stages_at = p.lat.nstages;
+  st.slots_a = p.la.nslots;
+  st.slots_at = p.lat.nslots;
+  st.bytes_a = p.la.bytes;
+  st.bytes_at = p.lat.bytes;
+  st.plan_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  return XCT_OK;
+}
+
+// ---------------------------------------------------------------------------
+// export (verification): canonical natural-order CSR on the host
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct Coo { int32_t r, c; double v; };
+
+xct_status to_canonical(std::vector<Coo>& coo, int64_t nrows, int64_t* rowptr, int32_t* col,
+                        double* val, int64_t* nnz) {
+  std::sort(coo.begin(), coo.end(), [](const Coo& a, const Coo& b) {
+    return a.r != b.r ? a.r < b.r : a.c < b.c;
+  });
+  *nnz = (int64_t)coo.size();
+  if (!rowptr) return XCT_OK;
+  for (int64_t r = 0; r <= nrows; ++r) rowptr[r] = 0;
+  for (size_t i = 0; i < coo.size(); ++i) {
+    rowptr[coo[i].r + 1]++;
+    col[i] = coo[i].c;
+    val[i] = coo[i].v;
+  }
+  for (int64_t r = 0; r < nrows; ++r) rowptr[r + 1] += rowptr[r];
+  return XCT_OK;
+}
+
+template <class T>
+xct_status d2h(std::vector<T>& h, const T* d, int64_t n) {
+  h.resize((size_t)std::max<int64_t>(n, 0));
+  if (n > 0) XCT_TRY_CUDA(cudaMemcpy(h.data(), d, sizeof(T) * n, cudaMemcpyDeviceToHost));
+  return XCT_OK;
+}
+
+}  // namespace
+
+xct_status export_matrix(Plan& p, int what, int64_t* rowptr, int32_t* col, double* val,
+                         int64_t* nnz) {
+  const bool tr = (what == XCT_EXPORT_AT_F64 || what == XCT_EXPORT_AT_STORED);
+  const int64_t nrows = tr ? p.npix : p.nray;
+  std::vector<int32_t> row_inv, col_inv;  // ordered id -> natural id
+  XCT_TRY(d2h(row_inv, tr ? p.pix_inv : p.ray_inv, nrows));
+  XCT_TRY(d2h(col_inv, tr ? p.ray_inv : p.pix_inv, tr ? p.nray : p.npix));
+  std::vector<Coo> coo;
+  if (what == XCT_EXPORT_A_F64 || what == XCT_EXPORT_AT_F64) {
+    if (!(p.flags & XCT_PLAN_KEEP_F64)) {
+      set_error("FP64 export needs a plan built with XCT_PLAN_KEEP_F64");
+      return XCT_ERR_INVALID;
+    }
+    std::vector<int64_t> rp;
+    std::vector<int32_t> cc;
+    std::vector<double> vv;
+    XCT_TRY(d2h(rp, tr ? p.t_rowptr : p.a_rowptr, nrows + 1));
+    XCT_TRY(d2h(cc, tr ? p.t_col : p.a_col, p.nnz));
+    XCT_TRY(d2h(vv, tr ? p.t_val : p.a_val, p.nnz));
+    coo.reserve((size_t)p.nnz);
+    for (int64_t r = 0; r < nrows; ++r)
+      for (int64_t e = rp[r]; e < rp[r + 1]; ++e) coo.push_back({row_inv[r], col_inv[cc[e]], vv[e]});
+  } else {
+    const Layout& L = tr ? p.lat : p.la;
+    std::vector<int64_t> bs, sp;
+    std::vector<int32_t> px;
+    std::vector<Seg> sg;
+    XCT_TRY(d2h(bs, L.blk_stage, (int64_t)L.nblocks + 1));
+    XCT_TRY(d2h(sp, L.stage_pix, L.nstages + 1));
+    XCT_TRY(d2h(px, L.pix, L.footprint));
+    XCT_TRY(d2h(sg, L.seg, L.nstages * kQuads));
+    std::vector<uint32_t> e4;
+    std::vector<unsigned long long> e8;
+    if (L.ebytes == 4) XCT_TRY(d2h(e4, static_cast<const uint32_t*>(L.ent), L.nslots));
+    else XCT_TRY(d2h(e8, static_cast<const unsigned long long*>(L.ent), L.nslots));
+    const double unscale = ldexp(1.0, -p.mat_scale_exp);
+    for (int32_t b = 0; b < L.nblocks; ++b) {
+      for (int64_t st = bs[b]; st < bs[b + 1]; ++st) {
+        for (int q = 0; q < kQuads; ++q) {
+          const Seg& s = sg[st * kQuads + q];
+          for (int g = 0; g < 4; ++g) {
+            int64_t row = (int64_t)b * kRowsPerBlock + q * 4 + g;
+            for (int k = 0; k < s.cnt[g]; ++k) {
+              int64_t slot = s.off + (k >> 2) * 16 + g * 4 + (k & 3);
+              uint32_t idx;
+              double v;
+              if (L.ebytes == 4) {
+                uint32_t w = e4[slot];
+                idx = w & 0xffffu;
+                uint16_t h = (uint16_t)(w >> 16);
+                if (p.storage == XCT_F16) {
+                  __half_raw hr;
+                  hr.x = h;
+                  v = (double)__half2float(__half(hr));
+                } else {
+                  uint32_t f = (uint32_t)h << 16;
+                  float ff;
+                  memcpy(&ff, &f, 4);
+                  v = ff;
+                }
+              } else {
+                unsigned long long w = e8[slot];
+                idx = (uint32_t)(w & 0xffffffffu);
+                uint32_t f = (uint32_t)(w >> 32);
+                float ff;
+                memcpy(&ff, &f, 4);
+                v = ff;
+              }
+              if (idx >= (uint32_t)(sp[st + 1] - sp[st]) || row >= nrows) {
+                set_error("packed layout holds an out-of-range entry (block %d stage %lld)", b,
+                          (long long)st);
+                return XCT_ERR_CUDA;
+              }
+              int32_t c = px[sp[st] + idx];
+              coo.push_back({row_inv[row], col_inv[c], v * unscale});
+            }
+          }
+        }
+      }
+    }
+  }
+  return to_canonical(coo, nrows, rowptr, col, val, nnz);
+}
+
+}  // namespace xct

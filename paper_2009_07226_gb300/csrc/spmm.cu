@@ -1,0 +1,406 @@
+// The fused projection / back-projection product Y = M X for a batch of
+// slices sharing the sparse matrix M (A or A^T) -- paper Sec. III-B.
+//
+// Design on sm_103a (what differs from Listing 1, written for V100):
+//   * input buffering (Sec. III-B1, III-B4): a block owns 64 consecutive rows
+//     in Hilbert order; their footprint (the distinct input rows they touch)
+//     is split into stages of `cap` vectors that are gathered into shared
+//     memory once per stage and reused by every row of the block;
+//   * register reuse (Sec. III-B2) is taken over slices: the lanes of a group
+//     hold different slices of the same row, so one packed entry feeds
+//     ST FMAs and every shared-memory wavefront reads one contiguous 128-byte
+//     staged vector (no bank conflicts), instead of one thread per row doing
+//     random 16-byte gathers;
+//   * output buffering (Sec. III-B3): per-lane FP32 accumulators, written
+//     once, with the per-slice squared norm reduced in the epilogue (the CGLS
+//     dot product, FP64);
+//   * packing (Sec. III-C2): {u16 stage index, 16-bit value} entries (4 bytes)
+//     for mixed precision, {u32 index, f32 value} (8 bytes) for FP32; four
+//     entries per 16-byte vector load, broadcast to the lanes of a group;
+//   * mixed precision (Sec. III-C): 16-bit values times 16-bit staged inputs
+//     accumulate in FP32 through the mixed-precision FMA (fma.rn.f32.f16 /
+//     .bf16, sm_100+); normalisation by 2^-e per slice during staging,
+//     de-normalisation by 2^(e-k) in the epilogue.
+#include "xct_internal.cuh"
+
+namespace xct {
+namespace {
+
+template <class TX> struct XBytes;
+template <> struct XBytes<float> { static constexpr int v = 4; };
+template <> struct XBytes<__half> { static constexpr int v = 2; };
+template <> struct XBytes<__nv_bfloat16> { static constexpr int v = 2; };
+
+template <class TX, int ST>
+struct Cfg {
+  static constexpr int XB = XBytes<TX>::v;
+  static constexpr int PIXB = ST * XB;                     // staged bytes per input row
+  static constexpr int VB = PIXB >= 16 ? 16 : PIXB;        // bytes per lane load
+  static constexpr int LPR = PIXB >= 128 ? 8 : PIXB / VB;  // lanes per matrix row
+  static constexpr int VPL = PIXB / (VB * LPR);            // loads per lane per entry
+  static constexpr int EPV = VB / XB;                      // elements per load
+  static constexpr int SPL = EPV * VPL;                    // slices per lane
+  static constexpr int RPW = 32 / LPR;                     // matrix rows per warp
+  static constexpr int NWARPS = kRowsPerBlock / RPW;
+  static constexpr int NT = NWARPS * 32;
+  static constexpr bool E16 = XB == 2;
+  // staging unit: 16 bytes of shared memory (or the whole row when smaller)
+  static constexpr int UB = PIXB >= 16 ? 16 : PIXB;
+  static constexpr int UPP = PIXB / UB;                    // units per staged row
+  static constexpr int EPU = UB / XB;                      // elements per unit
+  static constexpr int MIN_BLOCKS = (PIXB <= 128) ? 2 : 1;
+  __host__ __device__ static size_t stage_bytes(int cap) {
+    return (((size_t)cap + 1) * PIXB + 15) / 16 * 16;
+  }
+  static size_t smem_bytes(int cap) {
+    size_t a = stage_bytes(cap) + 2 * ST * sizeof(float);
+    size_t red = (size_t)NWARPS * ST * sizeof(double) + 2 * ST * sizeof(float);
+    return a > red ? a : red;
+  }
+};
+
+// --- shared memory vector load of VB bytes ---------------------------------
+template <int VB> struct VecT;
+template <> struct VecT<16> { using T = uint4; };
+template <> struct VecT<8> { using T = uint2; };
+template <> struct VecT<4> { using T = uint32_t; };
+template <> struct VecT<2> { using T = uint16_t; };
+
+// --- fused multiply-add of a staged vector ---------------------------------
+template <class TX, int EPV> struct Fma;
+
+template <int EPV>
+struct Fma<float, EPV> {
+  template <class V>
+  static __device__ __forceinline__ void run(float* acc, const V& v, uint32_t wbits) {
+    const float w = __uint_as_float(wbits);
+    const float* x = reinterpret_cast<const float*>(&v);
+#pragma unroll
+    for (int e = 0; e < EPV; ++e) acc[e] = fmaf(w, x[e], acc[e]);
+  }
+};
+
+template <int EPV>
+struct Fma<__half, EPV> {
+  template <class V>
+  static __device__ __forceinline__ void run(float* acc, const V& v, uint32_t wbits) {
+    const unsigned short w = (unsigned short)wbits;
+    if constexpr (EPV == 1) {
+      const unsigned short x = *reinterpret_cast<const unsigned short*>(&v);
+      asm("fma.rn.f32.f16 %0, %1, %2, %0;" : "+f"(acc[0]) : "h"(x), "h"(w));
+    } else {
+      const uint32_t* x = reinterpret_cast<const uint32_t*>(&v);
+#pragma unroll
+      for (int e = 0; e < EPV / 2; ++e) {
+        asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+            "fma.rn.f32.f16 %0, lo, %3, %0;\n\tfma.rn.f32.f16 %1, hi, %3, %1;\n\t}"
+            : "+f"(acc[2 * e]), "+f"(acc[2 * e + 1])
+            : "r"(x[e]), "h"(w));
+      }
+    }
+  }
+};
+
+template <int EPV>
+struct Fma<__nv_bfloat16, EPV> {
+  template <class V>
+  static __device__ __forceinline__ void run(float* acc, const V& v, uint32_t wbits) {
+    const unsigned short w = (unsigned short)wbits;
+    if constexpr (EPV == 1) {
+      const unsigned short x = *reinterpret_cast<const unsigned short*>(&v);
+      asm("fma.rn.f32.bf16 %0, %1, %2, %0;" : "+f"(acc[0]) : "h"(x), "h"(w));
+    } else {
+      const uint32_t* x = reinterpret_cast<const uint32_t*>(&v);
+#pragma unroll
+      for (int e = 0; e < EPV / 2; ++e) {
+        asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+            "fma.rn.f32.bf16 %0, lo, %3, %0;\n\tfma.rn.f32.bf16 %1, hi, %3, %1;\n\t}"
+            : "+f"(acc[2 * e]), "+f"(acc[2 * e + 1])
+            : "r"(x[e]), "h"(w));
+      }
+    }
+  }
+};
+
+// --- conversion of staged inputs -------------------------------------------
+template <class TX> __device__ __forceinline__ uint16_t to16(float v);
+template <> __device__ __forceinline__ uint16_t to16<__half>(float v) {
+  return __half_as_ushort(__float2half_rn(v));
+}
+template <> __device__ __forceinline__ uint16_t to16<__nv_bfloat16>(float v) {
+  return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+// per-slice normalisation exponent e = ceil(log2 m) (0 for m = 0)
+__device__ __forceinline__ int ceil_log2_exp(float m) {
+  if (!(m > 0.0f)) return 0;
+  int ex;
+  float f = frexpf(m, &ex);  // m = f * 2^ex, f in [0.5, 1)
+  return f == 0.5f ? ex - 1 : ex;
+}
+
+template <class TX, int ST>
+__global__ void __launch_bounds__(Cfg<TX, ST>::NT, Cfg<TX, ST>::MIN_BLOCKS)
+    spmm_kernel(const int64_t* __restrict__ blk_stage, const int64_t* __restrict__ stage_pix,
+                const int32_t* __restrict__ pix, const Seg* __restrict__ seg,
+                const void* __restrict__ ent, int64_t nrows, int64_t ncols, int cap,
+                const float* __restrict__ xin, float* __restrict__ yout,
+                const uint32_t* __restrict__ in_max, int mat_scale_exp,
+                double* __restrict__ dot_partial) {
+  using C = Cfg<TX, ST>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int tid = threadIdx.x;
+  const int b = blockIdx.x;
+  const int tile = blockIdx.y;
+  const int nblocks = gridDim.x;
+  float* sc = reinterpret_cast<float*>(smem + C::stage_bytes(cap));  // [ST] in, [ST] out
+  const float* xt = xin + (size_t)tile * ncols * ST;
+
+  // per-slice scales
+  for (int i = tid; i < ST; i += C::NT) {
+    if (C::E16) {
+      const int e = ceil_log2_exp(__uint_as_float(in_max[tile * ST + i]));
+      sc[i] = ldexpf(1.0f, -e);
+      sc[ST + i] = ldexpf(1.0f, e - mat_scale_exp);
+    } else {
+      sc[i] = 1.0f;
+      sc[ST + i] = 1.0f;
+    }
+  }
+  // zero slot (index cap) for padding entries
+  for (int i = tid; i < C::PIXB; i += C::NT) smem[(size_t)cap * C::PIXB + i] = 0;
+  __syncthreads();
+
+  const int warp = tid >> 5, lane = tid & 31;
+  const int rw = lane / C::LPR, sub = lane % C::LPR;
+  const int rb = warp * C::RPW + rw;
+  const int quad = rb >> 2, gq = rb & 3;
+
+  float acc[C::SPL];
+#pragma unroll
+  for (int i = 0; i < C::SPL; ++i) acc[i] = 0.0f;
+
+  const int64_t s0 = blk_stage[b], s1 = blk_stage[b + 1];
+  for (int64_t s = s0; s < s1; ++s) {
+    // ---- stage the footprint vectors ----
+    const int64_t p0 = stage_pix[s];
+    const int np = (int)(stage_pix[s + 1] - p0);
+    for (int i = tid; i < np * C::UPP; i += C::NT) {
+      const int p = i / C::UPP, u = i % C::UPP;
+      const float* src = xt + (size_t)pix[p0 + p] * ST + u * C::EPU;
+      unsigned char* dst = smem + (size_t)p * C::PIXB + u * C::UB;
+      if constexpr (!C::E16) {
+        if constexpr (C::UB == 16) {
+          *reinterpret_cast<float4*>(dst) = __ldg(reinterpret_cast<const float4*>(src));
+        } else if constexpr (C::UB == 8) {
+          *reinterpret_cast<float2*>(dst) = __ldg(reinterpret_cast<const float2*>(src));
+        } else {
+          *reinterpret_cast<float*>(dst) = __ldg(src);
+        }
+      } else {
+        float v[C::EPU];
+        if constexpr (C::EPU >= 4) {
+#pragma unroll
+          for (int q = 0; q < C::EPU / 4; ++q) {
+            float4 f = __ldg(reinterpret_cast<const float4*>(src) + q);
+            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < C::EPU; ++q) v[q] = __ldg(src + q);
+        }
+        uint16_t h[C::EPU];
+#pragma unroll
+        for (int q = 0; q < C::EPU; ++q) h[q] = to16<TX>(v[q] * sc[u * C::EPU + q]);
+        if constexpr (C::UB == 16) {
+          uint4 w;
+          w.x = h[0] | ((uint32_t)h[1] << 16); w.y = h[2] | ((uint32_t)h[3] << 16);
+          w.z = h[4] | ((uint32_t)h[5] << 16); w.w = h[6] | ((uint32_t)h[7] << 16);
+          *reinterpret_cast<uint4*>(dst) = w;
+        } else if constexpr (C::UB == 8) {
+          uint2 w;
+          w.x = h[0] | ((uint32_t)h[1] << 16); w.y = h[2] | ((uint32_t)h[3] << 16);
+          *reinterpret_cast<uint2*>(dst) = w;
+        } else if constexpr (C::UB == 4) {
+          *reinterpret_cast<uint32_t*>(dst) = h[0] | ((uint32_t)h[1] << 16);
+        } else {
+          *reinterpret_cast<uint16_t*>(dst) = h[0];
+        }
+      }
+    }
+    __syncthreads();
+
+    // ---- multiply: this lane group's row, this stage ----
+    const Seg sg = seg[s * kQuads + quad];
+    const int cnt = sg.cnt[gq];
+    const unsigned char* sbase = smem + sub * C::VB;
+    if constexpr (C::E16) {
+      const uint4* ep = reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(ent) + sg.off) + gq;
+      uint4 nxt = cnt > 0 ? __ldg(ep) : make_uint4(0, 0, 0, 0);
+      for (int k = 0; k < cnt; k += 4) {
+        const uint4 cur = nxt;
+        if (k + 4 < cnt) nxt = __ldg(ep + ((k >> 2) + 1) * 4);
+        const uint32_t e4[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (k + q < cnt) {
+            const uint32_t w = e4[q];
+            const unsigned char* xs = sbase + (size_t)(w & 0xffffu) * C::PIXB;
+#pragma unroll
+            for (int v = 0; v < C::VPL; ++v) {
+              const typename VecT<C::VB>::T xv =
+                  *reinterpret_cast<const typename VecT<C::VB>::T*>(xs + v * C::LPR * C::VB);
+              Fma<TX, C::EPV>::run(acc + v * C::EPV, xv, w >> 16);
+            }
+          }
+        }
+      }
+    } else {
+      const uint4* ep =
+          reinterpret_cast<const uint4*>(static_cast<const unsigned long long*>(ent) + sg.off) + gq * 2;
+      uint4 na = make_uint4(0, 0, 0, 0), nb = na;
+      if (cnt > 0) { na = __ldg(ep); nb = __ldg(ep + 1); }
+      for (int k = 0; k < cnt; k += 4) {
+        const uint4 ca = na, cb = nb;
+        if (k + 4 < cnt) {
+          const uint4* np2 = ep + ((k >> 2) + 1) * 8;
+          na = __ldg(np2);
+          nb = __ldg(np2 + 1);
+        }
+        const uint32_t idx[4] = {ca.x, ca.z, cb.x, cb.z};
+        const uint32_t val[4] = {ca.y, ca.w, cb.y, cb.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (k + q < cnt) {
+            const unsigned char* xs = sbase + (size_t)idx[q] * C::PIXB;
+#pragma unroll
+            for (int v = 0; v < C::VPL; ++v) {
+              const typename VecT<C::VB>::T xv =
+                  *reinterpret_cast<const typename VecT<C::VB>::T*>(xs + v * C::LPR * C::VB);
+              Fma<TX, C::EPV>::run(acc + v * C::EPV, xv, val[q]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- epilogue: de-normalise, write, per-slice squared norms ----
+  const int64_t row = (int64_t)b * kRowsPerBlock + rb;
+  float* yt = yout + (size_t)tile * nrows * ST;
+#pragma unroll
+  for (int v = 0; v < C::VPL; ++v) {
+#pragma unroll
+    for (int e = 0; e < C::EPV; ++e) {
+      const int sl = v * C::LPR * C::EPV + sub * C::EPV + e;
+      acc[v * C::EPV + e] *= sc[ST + sl];
+    }
+    if (row < nrows) {
+      float* dst = yt + (size_t)row * ST + v * C::LPR * C::EPV + sub * C::EPV;
+      if constexpr (C::EPV % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < C::EPV / 4; ++q)
+          reinterpret_cast<float4*>(dst)[q] =
+              make_float4(acc[v * C::EPV + 4 * q], acc[v * C::EPV + 4 * q + 1],
+                          acc[v * C::EPV + 4 * q + 2], acc[v * C::EPV + 4 * q + 3]);
+      } else if constexpr (C::EPV == 2) {
+        *reinterpret_cast<float2*>(dst) = make_float2(acc[v * C::EPV], acc[v * C::EPV + 1]);
+      } else {
+        dst[0] = acc[v * C::EPV];
+      }
+    }
+  }
+  if (dot_partial != nullptr) {
+    double* red = reinterpret_cast<double*>(smem);  // stage buffer is free now
+    double d[C::SPL];
+#pragma unroll
+    for (int i = 0; i < C::SPL; ++i) d[i] = (double)acc[i] * (double)acc[i];
+    // lanes with the same `sub` hold the same slices: reduce over rows
+#pragma unroll
+    for (int o = C::LPR; o < 32; o <<= 1) {
+#pragma unroll
+      for (int i = 0; i < C::SPL; ++i) d[i] += __shfl_xor_sync(0xffffffffu, d[i], o);
+    }
+    if (rw == 0) {
+#pragma unroll
+      for (int v = 0; v < C::VPL; ++v)
+#pragma unroll
+        for (int e = 0; e < C::EPV; ++e)
+          red[warp * ST + v * C::LPR * C::EPV + sub * C::EPV + e] = d[v * C::EPV + e];
+    }
+    __syncthreads();
+    for (int sl = tid; sl < ST; sl += C::NT) {
+      double t = 0.0;
+      for (int w = 0; w < C::NWARPS; ++w) t += red[w * ST + sl];
+      dot_partial[(size_t)(tile * ST + sl) * nblocks + b] = t;
+    }
+  }
+}
+
+template <class TX, int ST>
+xct_status launch(const SpmmArgs& a, cudaStream_t s) {
+  using C = Cfg<TX, ST>;
+  const Layout& L = *a.L;
+  const size_t smem = C::smem_bytes(L.cap);
+  static bool configured = false;  // attribute set once per instance
+  if (!configured) {
+    XCT_TRY_CUDA(cudaFuncSetAttribute(spmm_kernel<TX, ST>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured = true;
+  }
+  if (L.nblocks == 0 || a.ntiles == 0) return XCT_OK;
+  dim3 grid((unsigned)L.nblocks, (unsigned)a.ntiles);
+  spmm_kernel<TX, ST><<<grid, C::NT, smem, s>>>(L.blk_stage, L.stage_pix, L.pix, L.seg, L.ent,
+                                                L.nrows, L.ncols, L.cap, a.x, a.y, a.in_max,
+                                                a.mat_scale_exp, a.dot_partial);
+  count_launch();
+  XCT_TRY_CUDA(cudaGetLastError());
+  return XCT_OK;
+}
+
+template <class TX>
+xct_status dispatch(const SpmmArgs& a, cudaStream_t s) {
+  switch (a.st) {
+    case 1: return launch<TX, 1>(a, s);
+    case 2: return launch<TX, 2>(a, s);
+    case 4: return launch<TX, 4>(a, s);
+    case 8: return launch<TX, 8>(a, s);
+    case 16: return launch<TX, 16>(a, s);
+    case 32: return launch<TX, 32>(a, s);
+    case 64: return launch<TX, 64>(a, s);
+    default:
+      set_error("slices per tile %d not supported", a.st);
+      return XCT_ERR_UNSUPPORTED;
+  }
+}
+
+}  // namespace
+
+bool spmm_supported(xct_dtype storage, int st) {
+  (void)storage;
+  return st == 1 || st == 2 || st == 4 || st == 8 || st == 16 || st == 32 || st == 64;
+}
+
+int pick_slices_per_tile(xct_dtype storage, int S) {
+  const int maxst = storage == XCT_F32 ? 32 : 64;
+  int st = 1;
+  while (st < S && st < maxst) st <<= 1;
+  return st;
+}
+
+xct_status spmm(const SpmmArgs& a, cudaStream_t s) {
+  if (a.L->cap > 65535) {
+    set_error("stage capacity %d exceeds the 16-bit index", a.L->cap);
+    return XCT_ERR_UNSUPPORTED;
+  }
+  switch (a.storage) {
+    case XCT_F32: return dispatch<float>(a, s);
+    case XCT_F16: return dispatch<__half>(a, s);
+    case XCT_BF16: return dispatch<__nv_bfloat16>(a, s);
+  }
+  set_error("unknown storage type");
+  return XCT_ERR_INVALID;
+}
+
+}  // namespace xct

@@ -1,0 +1,161 @@
+// Internal declarations of libxct.so (not part of the C-ABI).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <vector>
+
+#include "xct.h"
+
+namespace xct {
+
+// ---------------------------------------------------------------------------
+// errors, allocation, launch accounting
+// ---------------------------------------------------------------------------
+
+void set_error(const char* fmt, ...);
+extern std::atomic<int64_t> g_launches;
+inline void count_launch(int64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// Device allocation through the configured allocator (cudaMallocAsync by
+// default).  Returns nullptr and sets the error message on failure.
+void* dalloc(size_t bytes, cudaStream_t s);
+void dfree(void* p, size_t bytes, cudaStream_t s);
+
+#define XCT_TRY_CUDA(call)                                                   \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) {                                                 \
+      ::xct::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                       __FILE__, __LINE__);                                  \
+      return XCT_ERR_CUDA;                                                   \
+    }                                                                        \
+  } while (0)
+
+#define XCT_TRY(expr)                  \
+  do {                                 \
+    xct_status st_ = (expr);           \
+    if (st_ != XCT_OK) return st_;     \
+  } while (0)
+
+// A set of device allocations released together (in reverse order).
+struct Arena {
+  struct Item { void* p; size_t n; };
+  std::vector<Item> items;
+  cudaStream_t stream = nullptr;
+  explicit Arena(cudaStream_t s = nullptr) : stream(s) {}
+  Arena(const Arena&) = delete;
+  Arena& operator=(const Arena&) = delete;
+  ~Arena() { release(); }
+  template <class T>
+  xct_status get(T** out, size_t count) {
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 256;
+    void* p = dalloc(bytes, stream);
+    if (!p) { *out = nullptr; return XCT_ERR_OOM; }
+    items.push_back({p, bytes});
+    *out = static_cast<T*>(p);
+    return XCT_OK;
+  }
+  void release() {
+    for (size_t i = items.size(); i-- > 0;) dfree(items[i].p, items[i].n, stream);
+    items.clear();
+  }
+  // hand ownership of all items to another arena
+  void move_to(Arena& other) {
+    for (auto& it : items) other.items.push_back(it);
+    items.clear();
+  }
+};
+
+// ---------------------------------------------------------------------------
+// kernel layout of one matrix (A or A^T)
+// ---------------------------------------------------------------------------
+
+constexpr int kRowsPerBlock = 64;              // rows of one thread block
+constexpr int kQuads = kRowsPerBlock / 4;      // 4-row groups per block
+constexpr int kDefaultCapacity = 848;          // staged vectors per stage
+
+// One (stage, quad) segment: the entries of 4 consecutive rows interleaved in
+// chunks of 4 entries; `off` counts entries from the start of `ent`.
+struct __align__(16) Seg {
+  int64_t off;
+  uint16_t cnt[4];
+};
+
+struct Layout {
+  int64_t nrows = 0, ncols = 0;
+  int32_t nblocks = 0;
+  int32_t cap = 0;             // staged vectors per stage (the zero slot is `cap`)
+  int32_t ebytes = 0;          // 4: {u16 index, 16-bit value}; 8: {u32 index, f32}
+  int64_t nstages = 0;
+  int64_t nslots = 0;          // stored entries including padding
+  int64_t footprint = 0;       // staged vectors over all stages
+  int64_t* blk_stage = nullptr;   // [nblocks + 1] stage ranges of the blocks
+  int64_t* stage_pix = nullptr;   // [nstages + 1] offsets into pix
+  int32_t* pix = nullptr;         // staged input row ids, stage by stage
+  Seg* seg = nullptr;             // [nstages * kQuads]
+  void* ent = nullptr;            // packed entries
+  int64_t bytes = 0;
+};
+
+struct Plan {
+  xct_geometry g{};
+  std::vector<double> cs;       // host angle table [M][2]
+  xct_dtype storage = XCT_F32;
+  uint32_t flags = 0;
+  int device = 0;
+  int64_t nray = 0, npix = 0, nnz = 0;
+  int32_t* pix_order = nullptr;  // natural pixel -> ordered id
+  int32_t* pix_inv = nullptr;    // ordered id -> natural pixel
+  int32_t* ray_order = nullptr;
+  int32_t* ray_inv = nullptr;
+  Layout la, lat;
+  int32_t mat_scale_exp = 0;     // k: stored value = RN(l * 2^k)
+  // kept FP64 matrices (ordered ids), only with XCT_PLAN_KEEP_F64
+  int64_t* a_rowptr = nullptr; int32_t* a_col = nullptr; double* a_val = nullptr;
+  int64_t* t_rowptr = nullptr; int32_t* t_col = nullptr; double* t_val = nullptr;
+  Arena mem;                     // everything above lives here
+  xct_stats stats{};
+};
+
+// plan building (plan.cu)
+xct_status build_plan(Plan& p, cudaStream_t s);
+xct_status export_matrix(Plan& p, int what, int64_t* rowptr, int32_t* col,
+                         double* val, int64_t* nnz);
+
+// device exclusive scans (scan.cu): out[i] = sum_{j<i} in[j], out[n] = total
+xct_status exclusive_scan_i32(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
+xct_status exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// products (spmm.cu) on the internal vector layout [tile][rows][st] float32
+// ---------------------------------------------------------------------------
+
+struct SpmmArgs {
+  const Layout* L;
+  const float* x;          // input [ntiles][L->ncols][st]
+  float* y;                // output [ntiles][L->nrows][st]
+  int st;                  // slices per tile
+  int ntiles;
+  xct_dtype storage;
+  int mat_scale_exp;
+  const uint32_t* in_max;  // per slice max |x| bits (16-bit storage) [ntiles*st]
+  double* dot_partial;     // nullable: [nblocks][ntiles*st] sum of y^2 per block
+};
+xct_status spmm(const SpmmArgs& a, cudaStream_t s);
+bool spmm_supported(xct_dtype storage, int st);
+int pick_slices_per_tile(xct_dtype storage, int S);
+
+// vector kernels (vec.cu)
+xct_status to_internal(const float* nat, float* in, const int32_t* inv_order,
+                       int64_t rows, int S, int st, int ntiles, uint32_t* max_bits,
+                       cudaStream_t s);
+xct_status to_natural(const float* in, float* nat, const int32_t* inv_order,
+                      int64_t rows, int S, int st, int ntiles, cudaStream_t s);
+
+}  // namespace xct

@@ -1,0 +1,36 @@
+// CGLS vector kernels and scalars (vec.cu), used by the solver driver.
+#pragma once
+
+#include "xct_internal.cuh"
+
+namespace xct {
+
+constexpr int kVecThreads = 256;
+constexpr int kVecBlocks = 256;   // blocks per slice tile of the vector kernels
+
+// Per-slice CGLS state on the device (FP64 scalars), [S_pad] each.
+struct CglsScalars {
+  double* gamma;
+  double* alpha;
+  double* beta;
+  int* active;
+  int* active0;      // active after the initial back projection
+  uint32_t* max_r;   // max |r| bits (normalisation of the back projection input)
+  uint32_t* max_p;   // max |p| bits (normalisation of the projection input)
+};
+
+xct_status cgls_update_xr(float* x, const float* p, int64_t npix, float* r, const float* q,
+                          int64_t nray, int st, int ntiles, const CglsScalars& sc, double* rpart,
+                          cudaStream_t s);
+xct_status cgls_update_p(float* p, const float* sv, int64_t npix, int st, int ntiles,
+                         const CglsScalars& sc, cudaStream_t s);
+xct_status cgls_residual(float* r, const float* q, int64_t nray, int st, int ntiles,
+                         uint32_t* max_r, double* rpart, cudaStream_t s);
+xct_status cgls_init_scalars(const double* gpart, int nbg, const double* rpart,
+                             const CglsScalars& sc, double* log, int S_pad, cudaStream_t s);
+xct_status cgls_alpha(const double* dpart, int nbd, const CglsScalars& sc, int S_pad,
+                      cudaStream_t s);
+xct_status cgls_beta(const double* gpart, int nbg, const double* rpart, const CglsScalars& sc,
+                     double* log_k, int S_pad, cudaStream_t s);
+
+}  // namespace xct

@@ -1,0 +1,89 @@
+"""Parity at the benchmark's full size (512^2 grid, 768 angles, 512 bins,
+64 slices) in the launch configuration the benchmark times (slice tiles of
+64 for 16-bit storage, 32 for FP32).  The oracle computes sampled outputs
+one by one: projections of sampled rays and back projections of sampled
+pixels (matrix-free), and the full FP64 CGLS of two sampled slices."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2009_07226_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+N, M, ND, S = 512, 768, 512, 64
+
+
+@pytest.fixture(scope="module")
+def xct():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_07226_gb300 import xct as x
+    return x
+
+
+@pytest.fixture(scope="module")
+def setup():
+    cs = inputs.angle_table(M)
+    g = oracle.Geometry(n=N, m=M, nd=ND, cos_sin=cs)
+    rng = np.random.default_rng(12)
+    x = rng.uniform(0, 1, size=(S, N * N)).astype(np.float32)
+    y = rng.uniform(0, 1, size=(S, M * ND)).astype(np.float32)
+    rays = np.sort(rng.choice(M * ND, 384, replace=False))
+    pixels = np.sort(rng.choice(N * N, 96, replace=False))
+    x64, y64 = x.astype(np.float64), y.astype(np.float64)
+    ref_y = oracle.project_rays(g, x64, rays)          # [S, 384]
+    ref_x = oracle.backproject_pixels(g, y64, pixels)  # [S, 96]
+    return g, x, y, rays, pixels, ref_y, ref_x
+
+
+@pytest.mark.parametrize("kind", ["f32", "f16", "bf16"])
+def test_products_sampled(xct, setup, kind):
+    g, x, y, rays, pixels, ref_y, ref_x = setup
+    with xct.Plan(N, M, ND, kind, cos_sin=g.table()) as p:
+        yo = p.project(torch.tensor(x.reshape(S, N, N), device="cuda"))
+        xo = p.backproject(torch.tensor(y.reshape(S, M, ND), device="cuda"))
+        torch.cuda.synchronize()
+    gy = yo.reshape(S, -1)[:, torch.tensor(rays, device="cuda")].double().cpu().numpy()
+    gx = xo.reshape(S, -1)[:, torch.tensor(pixels, device="cuda")].double().cpu().numpy()
+    if kind == "f32":
+        # lengths are positive and inputs non-negative: |a x| sums = the outputs
+        for got, ref in ((gy, ref_y), (gx, ref_x)):
+            assert np.linalg.norm(got - ref) / np.linalg.norm(ref) <= 1e-5
+            assert np.all(np.abs(got - ref) <= 1e-5 * ref + 1e-30)
+    else:
+        u = 2.0 ** -11 if kind == "f16" else 2.0 ** -8
+        for got, ref in ((gy, ref_y), (gx, ref_x)):
+            for s in range(S):
+                assert np.linalg.norm(got[s] - ref[s]) / np.linalg.norm(ref[s]) < u
+
+
+@pytest.mark.slow
+def test_cgls_sampled_slices(xct):
+    """The benchmark's CGLS (64 noisy slices, 50 iterations): slices 0 and
+    63 of the batched GPU solve against the FP64 oracle's solve of those
+    slices alone (slices are independent problems)."""
+    w = inputs.make_workload("batch3d_512", with_images=False)
+    K = w["iters"]
+    g = oracle.Geometry(n=N, m=M, nd=ND, cos_sin=w["cos_sin"])
+    a = oracle.siddon_csr(g)
+    at = oracle.transpose(a)
+    pick = [0, S - 1]
+    b = w["sino"].reshape(S, -1)
+    xo, logo = oracle.cgls(lambda X: oracle.project(a, X), lambda Y: oracle.backproject(at, Y),
+                           b[pick], K)
+    del a, at
+    bt = torch.tensor(w["sino"], dtype=torch.float32, device="cuda")
+    res = {}
+    for kind in ("f32", "f16"):
+        with xct.Plan(N, M, ND, kind, cos_sin=w["cos_sin"]) as p:
+            x, log = p.cgls(bt, K, resid=True)
+        res[kind] = (x.reshape(S, -1)[pick].double().cpu().numpy(), log.cpu().numpy())
+    err32 = np.linalg.norm(res["f32"][0] - xo) / np.linalg.norm(xo)
+    err16 = np.linalg.norm(res["f16"][0] - xo) / np.linalg.norm(xo)
+    assert err32 <= 1e-4, err32
+    assert err16 <= 1e-3, err16
+    l32, l16 = res["f32"][1], res["f16"][1]
+    assert np.max(np.abs(l16[:, :, 0] / l32[:, :, 0] - 1)) <= 0.01
+    np.testing.assert_allclose(l32[:, pick, 0], logo[:, :, 0], rtol=1e-3)
