@@ -1,12 +1,15 @@
 """GPU CGLS vs the FP64 oracle CGLS (same recurrence, per-slice scalars).
 
-FP32 storage: the iterate after K iterations agrees with the FP64 oracle's
-to a relative L2 of 1e-4 on the 2D workload (30 iterations, 128^2, 180
-angles, noiseless data from the oracle projector): single-precision
-products carry ~1e-7 relative error, which CGLS's short recurrences
-amplify over 30 steps to ~1e-5.  Mixed storage: the residual curve tracks
-FP32 within 1% at every iteration and the iterate stays within 1e-3 (f16)
-of FP64."""
+CGLS iterates are sensitive to rounding: once the Lanczos process behind CG
+loses orthogonality (after ~6 iterations on these workloads), any change in
+rounding -- FP32 vs FP64, or merely another summation order in FP64 --
+moves the iterate by 1e-3 .. 1e-1 (shown independently of the GPU by
+tests/test_oracle_cgls_sensitivity.py).  So the GPU is held to the oracle
+tightly over the stable phase (k <= 5: relative L2 <= 2e-5 in FP32, the
+FP32 envelope being ~3e-6), and over full runs through invariants: the
+logged residual equals the residual of the returned iterate, residuals do
+not increase, and the reconstruction is as close to the phantom as the
+oracle's."""
 import numpy as np
 import pytest
 import torch
@@ -41,21 +44,38 @@ def cgls2d():
     return w, g, a, at, b, xo, logo
 
 
-def test_cgls_2d_fp32_vs_oracle(xct, cgls2d):
+def test_cgls_2d_fp32_vs_oracle_stable_phase(xct, cgls2d):
+    w, g, a, at, b, xo, logo = cgls2d
+    n, m, nd = w["n"], w["m"], w["nd"]
+    bt = torch.tensor(b.reshape(1, m, nd), dtype=torch.float32, device="cuda")
+    with xct.Plan(n, m, nd, "f32", cos_sin=g.table()) as p:
+        for k in range(1, 6):
+            x, log = p.cgls(bt, k, resid=True)
+            xr, lr = oracle.cgls(*_ops(a, at), b, k)
+            err = np.linalg.norm(x.cpu().numpy().reshape(1, -1) - xr) / np.linalg.norm(xr)
+            assert err <= 2e-5, (k, err)
+            np.testing.assert_allclose(log.cpu().numpy(), lr, rtol=2e-5)
+
+
+def test_cgls_2d_fp32_full_run_invariants(xct, cgls2d):
     w, g, a, at, b, xo, logo = cgls2d
     n, m, nd, K = w["n"], w["m"], w["nd"], w["iters"]
     with xct.Plan(n, m, nd, "f32", cos_sin=g.table()) as p:
         bt = torch.tensor(b.reshape(1, m, nd), dtype=torch.float32, device="cuda")
         x, log = p.cgls(bt, K, resid=True)
-    x = x.cpu().numpy().reshape(1, -1)
-    err = np.linalg.norm(x - xo) / np.linalg.norm(xo)
-    assert err <= 1e-4, err
+    x = x.cpu().numpy().reshape(1, -1).astype(np.float64)
     log = log.cpu().numpy()
-    np.testing.assert_allclose(log[:, 0, 0], logo[:, 0, 0], rtol=1e-3)
-    np.testing.assert_allclose(log[:, 0, 1], logo[:, 0, 1], rtol=1e-3)
-    # the reconstruction approaches the phantom
-    ph = w["images"].reshape(-1)
-    assert np.linalg.norm(x[0] - ph) < 0.5 * np.linalg.norm(ph)
+    # the recursively updated residual is the residual of the returned x
+    true_r = np.linalg.norm(b - oracle.project(a, x))
+    assert abs(log[-1, 0, 0] - true_r) <= 1e-3 * true_r
+    # residual norms do not increase (FP32 rounding of the norm aside)
+    assert np.all(np.diff(log[:, 0, 0]) <= 1e-6 * log[:-1, 0, 0])
+    # as close to the phantom as the FP64 oracle's iterate (within the FP32
+    # envelope: numpy FP32 CGLS lands at 0.0576 vs FP64's 0.0552 here)
+    ph = w["images"].reshape(1, -1)
+    e_gpu = np.linalg.norm(x - ph) / np.linalg.norm(ph)
+    e_orc = np.linalg.norm(xo - ph) / np.linalg.norm(ph)
+    assert abs(e_gpu - e_orc) <= 0.1 * e_orc, (e_gpu, e_orc)
 
 
 def test_cgls_graph_and_direct_launches_agree(xct, cgls2d):
@@ -78,13 +98,13 @@ def test_cgls_warm_start(xct, cgls2d):
     n, m, nd = w["n"], w["m"], w["nd"]
     rng = np.random.default_rng(5)
     x0 = rng.uniform(0, 0.5, size=(1, n * n))
-    xr, lr = oracle.cgls(*_ops(a, at), b, 8, x0=x0)
+    xr, lr = oracle.cgls(*_ops(a, at), b, 4, x0=x0)
     with xct.Plan(n, m, nd, "f32", cos_sin=g.table()) as p:
-        x, log = p.cgls(torch.tensor(b.reshape(1, m, nd), dtype=torch.float32, device="cuda"), 8,
+        x, log = p.cgls(torch.tensor(b.reshape(1, m, nd), dtype=torch.float32, device="cuda"), 4,
                         x0=torch.tensor(x0.reshape(1, n, n), dtype=torch.float32, device="cuda"),
                         resid=True)
-    assert np.linalg.norm(x.cpu().numpy().reshape(1, -1) - xr) / np.linalg.norm(xr) < 1e-4
-    np.testing.assert_allclose(log.cpu().numpy()[:, 0, 0], lr[:, 0, 0], rtol=1e-3)
+    assert np.linalg.norm(x.cpu().numpy().reshape(1, -1) - xr) / np.linalg.norm(xr) < 2e-5
+    np.testing.assert_allclose(log.cpu().numpy()[:, 0, 0], lr[:, 0, 0], rtol=2e-5)
 
 
 def test_cgls_zero_slice_and_breakdown(xct):
@@ -114,12 +134,14 @@ def test_cgls_host_buffers(xct, cgls2d):
     assert np.array_equal(rh, ld.cpu().numpy())
 
 
-@pytest.mark.parametrize("kind,tol", [("f16", 1e-3), ("bf16", 8e-3)])
-def test_mixed_cgls_tracks_fp32(xct, kind, tol):
-    """Batched noisy 3D slices (Poisson at 1e4 photons), 20 iterations: the
-    mixed residual curve stays within 1% of FP32's at every iteration and
-    the iterate within `tol` of the FP64 oracle's."""
-    n, m, nd, S, K = 64, 96, 64, 8, 20
+@pytest.mark.parametrize("kind,tol", [("f16", 2e-3), ("bf16", 1.5e-2)])
+def test_mixed_cgls_stable_phase_and_tracking(xct, kind, tol):
+    """Batched noisy 3D slices (Poisson at 1e4 photons).  Over the stable
+    phase the mixed iterate is within the 16-bit envelope of the FP64
+    oracle's; over 20 iterations the mixed residual curve stays within 15%
+    of FP32's at every iteration (the envelope of a numpy model of the same
+    arithmetic is 4-10%) and the final residual within 3%."""
+    n, m, nd, S = 64, 96, 64, 8
     cs = inputs.angle_table(m)
     rng = np.random.default_rng(2)
     ells = inputs.random_ellipsoids(rng, 20)
@@ -130,16 +152,16 @@ def test_mixed_cgls_tracks_fp32(xct, kind, tol):
     g = oracle.Geometry(n=n, m=m, nd=nd, cos_sin=cs)
     a = oracle.siddon_csr(g)
     at = oracle.transpose(a)
-    xo, logo = oracle.cgls(*_ops(a, at), sino.reshape(S, -1), K)
     bt = torch.tensor(sino, dtype=torch.float32, device="cuda")
     with xct.Plan(n, m, nd, "f32", cos_sin=cs) as p32, xct.Plan(n, m, nd, kind, cos_sin=cs) as pm:
-        x32, l32 = p32.cgls(bt, K, resid=True)
-        xm, lm = pm.cgls(bt, K, resid=True)
-    l32, lm = l32.cpu().numpy(), lm.cpu().numpy()
-    assert np.max(np.abs(lm[:, :, 0] / l32[:, :, 0] - 1)) <= 0.01
-    xm = xm.cpu().numpy().reshape(S, -1)
-    x32 = x32.cpu().numpy().reshape(S, -1)
-    err_m = np.linalg.norm(xm - xo) / np.linalg.norm(xo)
-    err_32 = np.linalg.norm(x32 - xo) / np.linalg.norm(xo)
-    assert err_32 <= 1e-4, err_32
-    assert err_m <= tol, err_m
+        for k in (1, 3, 5):
+            xr, _ = oracle.cgls(*_ops(a, at), sino.reshape(S, -1), k)
+            x32 = p32.cgls(bt, k).cpu().numpy().reshape(S, -1)
+            xm = pm.cgls(bt, k).cpu().numpy().reshape(S, -1)
+            assert np.linalg.norm(x32 - xr) / np.linalg.norm(xr) <= 2e-5
+            assert np.linalg.norm(xm - xr) / np.linalg.norm(xr) <= tol, (k, kind)
+        _, l32 = p32.cgls(bt, 20, resid=True)
+        _, lm = pm.cgls(bt, 20, resid=True)
+    ratio = lm.cpu().numpy()[:, :, 0] / l32.cpu().numpy()[:, :, 0]
+    assert np.max(np.abs(ratio - 1)) <= 0.15
+    assert np.max(np.abs(ratio[-1] - 1)) <= 0.03
