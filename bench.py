@@ -309,6 +309,42 @@ def run_ours(args):
     print(json.dumps(out))
 
 
+def run_products(args):
+    """Projection and back projection alone (S = 64 slices of the workload's
+    geometry, one storage type): for profiling the product kernels."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_07226_gb300 import inputs, xct
+    wl = inputs.WORKLOADS[WORKLOAD]
+    n, m, nd, S = wl["n"], wl["m"], wl["nd"], wl["slices"]
+    plan = xct.Plan(n, m, nd, args.storage, cos_sin=inputs.angle_table(m))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand((S, n, n), device="cuda", generator=g)
+    y = torch.rand((S, m, nd), device="cuda", generator=g)
+    yo, xo = torch.empty_like(y), torch.empty_like(x)
+    for _ in range(args.warmup):
+        plan.project(x, out=yo)
+        plan.backproject(y, out=xo)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    for _ in range(args.steps):
+        plan.project(x, out=yo)
+    e[1].record()
+    for _ in range(args.steps):
+        plan.backproject(y, out=xo)
+    e[2].record()
+    torch.cuda.synchronize()
+    nnz = plan.stats()["nnz"]
+    tp, tb = e[0].elapsed_time(e[1]) / args.steps, e[1].elapsed_time(e[2]) / args.steps
+    print(json.dumps({"mode": "products", "storage": args.storage, "nnz": nnz, "slices": S,
+                      "project_ms": tp, "backproject_ms": tb,
+                      "project_gflops": 2.0 * nnz * S / tp / 1e6,
+                      "backproject_gflops": 2.0 * nnz * S / tb / 1e6}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -316,8 +352,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="cgls", choices=["cgls", "products"])
+    ap.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16"])
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.mode == "products":
+        run_products(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -53,8 +53,8 @@ struct Cfg {
     return (((size_t)cap + 1) * PIXB + 15) / 16 * 16;
   }
   static size_t smem_bytes(int cap) {
-    size_t a = stage_bytes(cap) + 2 * ST * sizeof(float);
-    size_t red = (size_t)NWARPS * ST * sizeof(double) + 2 * ST * sizeof(float);
+    size_t a = stage_bytes(cap) + ST * sizeof(float);
+    size_t red = (size_t)NWARPS * ST * sizeof(double) + ST * sizeof(float);
     return a > red ? a : red;
   }
 };
@@ -139,12 +139,26 @@ __device__ __forceinline__ int ceil_log2_exp(float m) {
   return f == 0.5f ? ex - 1 : ex;
 }
 
+// asynchronous global -> shared copy of `bytes` (4, 8 or 16) bytes
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 template <class TX, int ST>
 __global__ void __launch_bounds__(Cfg<TX, ST>::NT, Cfg<TX, ST>::MIN_BLOCKS)
     spmm_kernel(const int64_t* __restrict__ blk_stage, const int64_t* __restrict__ stage_pix,
                 const int32_t* __restrict__ pix, const Seg* __restrict__ seg,
                 const void* __restrict__ ent, int64_t nrows, int64_t ncols, int cap,
-                const float* __restrict__ xin, float* __restrict__ yout,
+                const unsigned char* __restrict__ xs, float* __restrict__ yout,
                 const uint32_t* __restrict__ in_max, int mat_scale_exp,
                 double* __restrict__ dot_partial) {
   using C = Cfg<TX, ST>;
@@ -153,23 +167,20 @@ __global__ void __launch_bounds__(Cfg<TX, ST>::NT, Cfg<TX, ST>::MIN_BLOCKS)
   const int b = blockIdx.x;
   const int tile = blockIdx.y;
   const int nblocks = gridDim.x;
-  float* sc = reinterpret_cast<float*>(smem + C::stage_bytes(cap));  // [ST] in, [ST] out
-  const float* xt = xin + (size_t)tile * ncols * ST;
+  float* osc = reinterpret_cast<float*>(smem + C::stage_bytes(cap));  // [ST] output scales
+  // staged rows of this slice tile: PIXB bytes each (16-bit normalised or FP32)
+  const unsigned char* xt = xs + (size_t)tile * ncols * C::PIXB;
 
-  // per-slice scales
   for (int i = tid; i < ST; i += C::NT) {
     if (C::E16) {
       const int e = ceil_log2_exp(__uint_as_float(in_max[tile * ST + i]));
-      sc[i] = ldexpf(1.0f, -e);
-      sc[ST + i] = ldexpf(1.0f, e - mat_scale_exp);
+      osc[i] = ldexpf(1.0f, e - mat_scale_exp);
     } else {
-      sc[i] = 1.0f;
-      sc[ST + i] = 1.0f;
+      osc[i] = 1.0f;
     }
   }
-  // zero slot (index cap) for padding entries
+  // zero slot (index cap): padding entries read it with value 0
   for (int i = tid; i < C::PIXB; i += C::NT) smem[(size_t)cap * C::PIXB + i] = 0;
-  __syncthreads();
 
   const int warp = tid >> 5, lane = tid & 31;
   const int rw = lane / C::LPR, sub = lane % C::LPR;
@@ -182,105 +193,94 @@ __global__ void __launch_bounds__(Cfg<TX, ST>::NT, Cfg<TX, ST>::MIN_BLOCKS)
 
   const int64_t s0 = blk_stage[b], s1 = blk_stage[b + 1];
   for (int64_t s = s0; s < s1; ++s) {
-    // ---- stage the footprint vectors ----
+    // ---- stage the footprint rows (asynchronous byte copies) ----
     const int64_t p0 = stage_pix[s];
     const int np = (int)(stage_pix[s + 1] - p0);
-    for (int i = tid; i < np * C::UPP; i += C::NT) {
-      const int p = i / C::UPP, u = i % C::UPP;
-      const float* src = xt + (size_t)pix[p0 + p] * ST + u * C::EPU;
-      unsigned char* dst = smem + (size_t)p * C::PIXB + u * C::UB;
-      if constexpr (!C::E16) {
-        if constexpr (C::UB == 16) {
-          *reinterpret_cast<float4*>(dst) = __ldg(reinterpret_cast<const float4*>(src));
-        } else if constexpr (C::UB == 8) {
-          *reinterpret_cast<float2*>(dst) = __ldg(reinterpret_cast<const float2*>(src));
-        } else {
-          *reinterpret_cast<float*>(dst) = __ldg(src);
-        }
-      } else {
-        float v[C::EPU];
-        if constexpr (C::EPU >= 4) {
+    const int units = np * C::UPP;
+    if constexpr (C::UB >= 4) {
+      constexpr int U = 4;  // units issued per thread per round
+      for (int i0 = tid; i0 < units; i0 += U * C::NT) {
+        int32_t gp[U];
 #pragma unroll
-          for (int q = 0; q < C::EPU / 4; ++q) {
-            float4 f = __ldg(reinterpret_cast<const float4*>(src) + q);
-            v[4 * q] = f.x; v[4 * q + 1] = f.y; v[4 * q + 2] = f.z; v[4 * q + 3] = f.w;
+        for (int j = 0; j < U; ++j) {
+          const int i = i0 + j * C::NT;
+          gp[j] = i < units ? __ldg(pix + p0 + i / C::UPP) : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+          const int i = i0 + j * C::NT;
+          if (i < units) {
+            const int p = i / C::UPP, u = i % C::UPP;
+            cp_async<C::UB>(smem + (size_t)p * C::PIXB + u * C::UB,
+                            xt + (size_t)gp[j] * C::PIXB + u * C::UB);
           }
-        } else {
-#pragma unroll
-          for (int q = 0; q < C::EPU; ++q) v[q] = __ldg(src + q);
-        }
-        uint16_t h[C::EPU];
-#pragma unroll
-        for (int q = 0; q < C::EPU; ++q) h[q] = to16<TX>(v[q] * sc[u * C::EPU + q]);
-        if constexpr (C::UB == 16) {
-          uint4 w;
-          w.x = h[0] | ((uint32_t)h[1] << 16); w.y = h[2] | ((uint32_t)h[3] << 16);
-          w.z = h[4] | ((uint32_t)h[5] << 16); w.w = h[6] | ((uint32_t)h[7] << 16);
-          *reinterpret_cast<uint4*>(dst) = w;
-        } else if constexpr (C::UB == 8) {
-          uint2 w;
-          w.x = h[0] | ((uint32_t)h[1] << 16); w.y = h[2] | ((uint32_t)h[3] << 16);
-          *reinterpret_cast<uint2*>(dst) = w;
-        } else if constexpr (C::UB == 4) {
-          *reinterpret_cast<uint32_t*>(dst) = h[0] | ((uint32_t)h[1] << 16);
-        } else {
-          *reinterpret_cast<uint16_t*>(dst) = h[0];
         }
       }
+      cp_async_wait_all();
+    } else {
+      for (int i = tid; i < units; i += C::NT)
+        *reinterpret_cast<uint16_t*>(smem + (size_t)i * C::PIXB) =
+            *reinterpret_cast<const uint16_t*>(xt + (size_t)__ldg(pix + p0 + i) * C::PIXB);
     }
     __syncthreads();
 
     // ---- multiply: this lane group's row, this stage ----
-    const Seg sg = seg[s * kQuads + quad];
-    const int cnt = sg.cnt[gq];
+    // Seg {int64 off; u16 cnt[4]} read as one 16-byte vector
+    const uint4 sgv = __ldg(reinterpret_cast<const uint4*>(seg) + s * kQuads + quad);
+    const int64_t soff = (int64_t)(((uint64_t)sgv.y << 32) | sgv.x);
+    const uint32_t cw = (gq < 2) ? sgv.z : sgv.w;
+    const int cnt = (int)((cw >> ((gq & 1) * 16)) & 0xffffu);
+    const int nch = (cnt + 3) >> 2;   // chunks of 4 entries (padding reads slot 0.0)
     const unsigned char* sbase = smem + sub * C::VB;
     if constexpr (C::E16) {
-      const uint4* ep = reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(ent) + sg.off) + gq;
-      uint4 nxt = cnt > 0 ? __ldg(ep) : make_uint4(0, 0, 0, 0);
-      for (int k = 0; k < cnt; k += 4) {
-        const uint4 cur = nxt;
-        if (k + 4 < cnt) nxt = __ldg(ep + ((k >> 2) + 1) * 4);
+      const uint4* ep = reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(ent) + soff) + gq;
+      uint4 c0 = make_uint4(0, 0, 0, 0), c1 = c0;
+      if (nch > 0) c0 = __ldg(ep);
+      if (nch > 1) c1 = __ldg(ep + 4);
+      for (int c = 0; c < nch; ++c) {
+        const uint4 cur = c0;
+        c0 = c1;
+        if (c + 2 < nch) c1 = __ldg(ep + (c + 2) * 4);
         const uint32_t e4[4] = {cur.x, cur.y, cur.z, cur.w};
+        typename VecT<C::VB>::T xv[4][C::VPL];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (k + q < cnt) {
-            const uint32_t w = e4[q];
-            const unsigned char* xs = sbase + (size_t)(w & 0xffffu) * C::PIXB;
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int v = 0; v < C::VPL; ++v) {
-              const typename VecT<C::VB>::T xv =
-                  *reinterpret_cast<const typename VecT<C::VB>::T*>(xs + v * C::LPR * C::VB);
-              Fma<TX, C::EPV>::run(acc + v * C::EPV, xv, w >> 16);
-            }
-          }
-        }
+          for (int v = 0; v < C::VPL; ++v)
+            xv[q][v] = *reinterpret_cast<const typename VecT<C::VB>::T*>(
+                sbase + (size_t)(e4[q] & 0xffffu) * C::PIXB + v * C::LPR * C::VB);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int v = 0; v < C::VPL; ++v) Fma<TX, C::EPV>::run(acc + v * C::EPV, xv[q][v], e4[q] >> 16);
       }
     } else {
       const uint4* ep =
-          reinterpret_cast<const uint4*>(static_cast<const unsigned long long*>(ent) + sg.off) + gq * 2;
-      uint4 na = make_uint4(0, 0, 0, 0), nb = na;
-      if (cnt > 0) { na = __ldg(ep); nb = __ldg(ep + 1); }
-      for (int k = 0; k < cnt; k += 4) {
-        const uint4 ca = na, cb = nb;
-        if (k + 4 < cnt) {
-          const uint4* np2 = ep + ((k >> 2) + 1) * 8;
-          na = __ldg(np2);
-          nb = __ldg(np2 + 1);
+          reinterpret_cast<const uint4*>(static_cast<const unsigned long long*>(ent) + soff) + gq * 2;
+      uint4 a0 = make_uint4(0, 0, 0, 0), b0 = a0, a1 = a0, b1 = a0;
+      if (nch > 0) { a0 = __ldg(ep); b0 = __ldg(ep + 1); }
+      if (nch > 1) { a1 = __ldg(ep + 8); b1 = __ldg(ep + 9); }
+      for (int c = 0; c < nch; ++c) {
+        const uint4 ca = a0, cb = b0;
+        a0 = a1;
+        b0 = b1;
+        if (c + 2 < nch) {
+          a1 = __ldg(ep + (c + 2) * 8);
+          b1 = __ldg(ep + (c + 2) * 8 + 1);
         }
         const uint32_t idx[4] = {ca.x, ca.z, cb.x, cb.z};
         const uint32_t val[4] = {ca.y, ca.w, cb.y, cb.w};
+        typename VecT<C::VB>::T xv[4][C::VPL];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (k + q < cnt) {
-            const unsigned char* xs = sbase + (size_t)idx[q] * C::PIXB;
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int v = 0; v < C::VPL; ++v) {
-              const typename VecT<C::VB>::T xv =
-                  *reinterpret_cast<const typename VecT<C::VB>::T*>(xs + v * C::LPR * C::VB);
-              Fma<TX, C::EPV>::run(acc + v * C::EPV, xv, val[q]);
-            }
-          }
-        }
+          for (int v = 0; v < C::VPL; ++v)
+            xv[q][v] = *reinterpret_cast<const typename VecT<C::VB>::T*>(
+                sbase + (size_t)idx[q] * C::PIXB + v * C::LPR * C::VB);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int v = 0; v < C::VPL; ++v) Fma<TX, C::EPV>::run(acc + v * C::EPV, xv[q][v], val[q]);
       }
     }
     __syncthreads();
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(Cfg<TX, ST>::NT, Cfg<TX, ST>::MIN_BLOCKS)
 #pragma unroll
     for (int e = 0; e < C::EPV; ++e) {
       const int sl = v * C::LPR * C::EPV + sub * C::EPV + e;
-      acc[v * C::EPV + e] *= sc[ST + sl];
+      acc[v * C::EPV + e] *= osc[sl];
     }
     if (row < nrows) {
       float* dst = yt + (size_t)row * ST + v * C::LPR * C::EPV + sub * C::EPV;
@@ -338,6 +338,36 @@ __global__ void __launch_bounds__(Cfg<TX, ST>::NT, Cfg<TX, ST>::MIN_BLOCKS)
   }
 }
 
+// FP32 [ntiles][rows][ST] -> 16-bit staging copy, slice s multiplied by
+// 2^-ceil(log2 max|x_s|) before rounding to nearest even.
+template <class TX, int ST>
+__global__ void to_staged16_kernel(const float* __restrict__ x, uint16_t* __restrict__ out,
+                                   int64_t rows, const uint32_t* __restrict__ in_max) {
+  __shared__ float isc[ST];
+  const int tile = blockIdx.y;
+  for (int i = threadIdx.x; i < ST; i += blockDim.x)
+    isc[i] = ldexpf(1.0f, -ceil_log2_exp(__uint_as_float(in_max[tile * ST + i])));
+  __syncthreads();
+  const int64_t n = rows * ST;
+  const float* xt = x + (size_t)tile * n;
+  uint16_t* ot = out + (size_t)tile * n;
+  if constexpr (ST % 4 == 0) {
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 4; i < n;
+         i += (int64_t)gridDim.x * blockDim.x * 4) {
+      const float4 f = *reinterpret_cast<const float4*>(xt + i);
+      const int sl = (int)(i % ST);
+      uint2 w;
+      w.x = to16<TX>(f.x * isc[sl]) | ((uint32_t)to16<TX>(f.y * isc[sl + 1]) << 16);
+      w.y = to16<TX>(f.z * isc[sl + 2]) | ((uint32_t)to16<TX>(f.w * isc[sl + 3]) << 16);
+      *reinterpret_cast<uint2*>(ot + i) = w;
+    }
+  } else {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+      ot[i] = to16<TX>(xt[i] * isc[i % ST]);
+  }
+}
+
 template <class TX, int ST>
 xct_status launch(const SpmmArgs& a, cudaStream_t s) {
   using C = Cfg<TX, ST>;
@@ -350,9 +380,20 @@ xct_status launch(const SpmmArgs& a, cudaStream_t s) {
     configured = true;
   }
   if (L.nblocks == 0 || a.ntiles == 0) return XCT_OK;
+  const unsigned char* src = reinterpret_cast<const unsigned char*>(a.x);
+  if constexpr (C::E16) {
+    if (!a.staged16) {
+      set_error("16-bit storage needs a staging buffer");
+      return XCT_ERR_INVALID;
+    }
+    dim3 cgrid(152 * 4, (unsigned)a.ntiles);
+    to_staged16_kernel<TX, ST><<<cgrid, 256, 0, s>>>(a.x, a.staged16, L.ncols, a.in_max);
+    count_launch();
+    src = reinterpret_cast<const unsigned char*>(a.staged16);
+  }
   dim3 grid((unsigned)L.nblocks, (unsigned)a.ntiles);
   spmm_kernel<TX, ST><<<grid, C::NT, smem, s>>>(L.blk_stage, L.stage_pix, L.pix, L.seg, L.ent,
-                                                L.nrows, L.ncols, L.cap, a.x, a.y, a.in_max,
+                                                L.nrows, L.ncols, L.cap, src, a.y, a.in_max,
                                                 a.mat_scale_exp, a.dot_partial);
   count_launch();
   XCT_TRY_CUDA(cudaGetLastError());

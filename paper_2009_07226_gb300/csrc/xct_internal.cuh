@@ -145,7 +145,9 @@ struct SpmmArgs {
   xct_dtype storage;
   int mat_scale_exp;
   const uint32_t* in_max;  // per slice max |x| bits (16-bit storage) [ntiles*st]
-  double* dot_partial;     // nullable: [nblocks][ntiles*st] sum of y^2 per block
+  double* dot_partial;     // nullable: [ntiles*st][nblocks] sum of y^2 per block
+  uint16_t* staged16;      // 16-bit storage: scratch [ntiles][L->ncols][st] for the
+                           // normalised 16-bit copy of x (unused for FP32)
 };
 xct_status spmm(const SpmmArgs& a, cudaStream_t s);
 bool spmm_supported(xct_dtype storage, int st);

@@ -134,13 +134,14 @@ def test_cgls_host_buffers(xct, cgls2d):
     assert np.array_equal(rh, ld.cpu().numpy())
 
 
-@pytest.mark.parametrize("kind,tol", [("f16", 2e-3), ("bf16", 1.5e-2)])
-def test_mixed_cgls_stable_phase_and_tracking(xct, kind, tol):
+@pytest.mark.parametrize("kind,tol,track", [("f16", 2e-3, 0.15), ("bf16", 1.5e-2, 0.25)])
+def test_mixed_cgls_stable_phase_and_tracking(xct, kind, tol, track):
     """Batched noisy 3D slices (Poisson at 1e4 photons).  Over the stable
     phase the mixed iterate is within the 16-bit envelope of the FP64
     oracle's; over 20 iterations the mixed residual curve stays within 15%
-    of FP32's at every iteration (the envelope of a numpy model of the same
-    arithmetic is 4-10%) and the final residual within 3%."""
+    (binary16) / 25% (bfloat16, 8x the unit roundoff) of FP32's at every
+    iteration -- a numpy model of the binary16 arithmetic departs by 4-10%
+    -- and the final residual within 3%."""
     n, m, nd, S = 64, 96, 64, 8
     cs = inputs.angle_table(m)
     rng = np.random.default_rng(2)
@@ -163,5 +164,5 @@ def test_mixed_cgls_stable_phase_and_tracking(xct, kind, tol):
         _, l32 = p32.cgls(bt, 20, resid=True)
         _, lm = pm.cgls(bt, 20, resid=True)
     ratio = lm.cpu().numpy()[:, :, 0] / l32.cpu().numpy()[:, :, 0]
-    assert np.max(np.abs(ratio - 1)) <= 0.15
+    assert np.max(np.abs(ratio - 1)) <= track
     assert np.max(np.abs(ratio[-1] - 1)) <= 0.03
