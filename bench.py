@@ -339,7 +339,11 @@ def run_products(args):
     torch.cuda.synchronize()
     nnz = plan.stats()["nnz"]
     tp, tb = e[0].elapsed_time(e[1]) / args.steps, e[1].elapsed_time(e[2]) / args.steps
+    st = plan.stats()
     print(json.dumps({"mode": "products", "storage": args.storage, "nnz": nnz, "slices": S,
+                      "stages_a": st["stages_a"], "stages_at": st["stages_at"],
+                      "slots_a": st["slots_a"], "slots_at": st["slots_at"],
+                      "bytes_a": st["bytes_a"], "bytes_at": st["bytes_at"],
                       "project_ms": tp, "backproject_ms": tb,
                       "project_gflops": 2.0 * nnz * S / tp / 1e6,
                       "backproject_gflops": 2.0 * nnz * S / tb / 1e6}))

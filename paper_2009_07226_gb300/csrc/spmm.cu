@@ -193,6 +193,26 @@ __global__ void __launch_bounds__(Cfg<TX, ST>::NT, Cfg<TX, ST>::MIN_BLOCKS)
 
   const int64_t s0 = blk_stage[b], s1 = blk_stage[b + 1];
   for (int64_t s = s0; s < s1; ++s) {
+    // ---- this group's segment header and first entry chunks: issued before
+    // the staging copies so their latency overlaps them ----
+    // Seg {int64 off; u16 cnt[4]} read as one 16-byte vector
+    const uint4 sgv = __ldg(reinterpret_cast<const uint4*>(seg) + s * kQuads + quad);
+    const int64_t soff = (int64_t)(((uint64_t)sgv.y << 32) | sgv.x);
+    const uint32_t cw = (gq < 2) ? sgv.z : sgv.w;
+    const int cnt = (int)((cw >> ((gq & 1) * 16)) & 0xffffu);
+    const int nch = (cnt + 3) >> 2;   // chunks of 4 entries (padding reads slot 0.0)
+    constexpr int PF = 3;             // chunks in flight
+    constexpr int CW = C::E16 ? 1 : 2;        // 16-byte words per chunk of one row
+    const uint4* ep = C::E16
+        ? reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(ent) + soff) + gq
+        : reinterpret_cast<const uint4*>(static_cast<const unsigned long long*>(ent) + soff) + gq * 2;
+    uint4 pf[PF][CW];
+#pragma unroll
+    for (int j = 0; j < PF; ++j)
+#pragma unroll
+      for (int w = 0; w < CW; ++w)
+        pf[j][w] = j < nch ? __ldg(ep + j * 4 * CW + w) : make_uint4(0, 0, 0, 0);
+
     // ---- stage the footprint rows (asynchronous byte copies) ----
     const int64_t p0 = stage_pix[s];
     const int np = (int)(stage_pix[s + 1] - p0);
@@ -225,63 +245,40 @@ __global__ void __launch_bounds__(Cfg<TX, ST>::NT, Cfg<TX, ST>::MIN_BLOCKS)
     __syncthreads();
 
     // ---- multiply: this lane group's row, this stage ----
-    // Seg {int64 off; u16 cnt[4]} read as one 16-byte vector
-    const uint4 sgv = __ldg(reinterpret_cast<const uint4*>(seg) + s * kQuads + quad);
-    const int64_t soff = (int64_t)(((uint64_t)sgv.y << 32) | sgv.x);
-    const uint32_t cw = (gq < 2) ? sgv.z : sgv.w;
-    const int cnt = (int)((cw >> ((gq & 1) * 16)) & 0xffffu);
-    const int nch = (cnt + 3) >> 2;   // chunks of 4 entries (padding reads slot 0.0)
     const unsigned char* sbase = smem + sub * C::VB;
-    if constexpr (C::E16) {
-      const uint4* ep = reinterpret_cast<const uint4*>(static_cast<const uint32_t*>(ent) + soff) + gq;
-      uint4 c0 = make_uint4(0, 0, 0, 0), c1 = c0;
-      if (nch > 0) c0 = __ldg(ep);
-      if (nch > 1) c1 = __ldg(ep + 4);
-      for (int c = 0; c < nch; ++c) {
-        const uint4 cur = c0;
-        c0 = c1;
-        if (c + 2 < nch) c1 = __ldg(ep + (c + 2) * 4);
-        const uint32_t e4[4] = {cur.x, cur.y, cur.z, cur.w};
-        typename VecT<C::VB>::T xv[4][C::VPL];
+    for (int c = 0; c < nch; ++c) {
+      uint4 cur[CW];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+      for (int w = 0; w < CW; ++w) cur[w] = pf[0][w];
 #pragma unroll
-          for (int v = 0; v < C::VPL; ++v)
-            xv[q][v] = *reinterpret_cast<const typename VecT<C::VB>::T*>(
-                sbase + (size_t)(e4[q] & 0xffffu) * C::PIXB + v * C::LPR * C::VB);
+      for (int j = 0; j + 1 < PF; ++j)
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
+        for (int w = 0; w < CW; ++w) pf[j][w] = pf[j + 1][w];
+      if (c + PF < nch) {
 #pragma unroll
-          for (int v = 0; v < C::VPL; ++v) Fma<TX, C::EPV>::run(acc + v * C::EPV, xv[q][v], e4[q] >> 16);
+        for (int w = 0; w < CW; ++w) pf[PF - 1][w] = __ldg(ep + (c + PF) * 4 * CW + w);
       }
-    } else {
-      const uint4* ep =
-          reinterpret_cast<const uint4*>(static_cast<const unsigned long long*>(ent) + soff) + gq * 2;
-      uint4 a0 = make_uint4(0, 0, 0, 0), b0 = a0, a1 = a0, b1 = a0;
-      if (nch > 0) { a0 = __ldg(ep); b0 = __ldg(ep + 1); }
-      if (nch > 1) { a1 = __ldg(ep + 8); b1 = __ldg(ep + 9); }
-      for (int c = 0; c < nch; ++c) {
-        const uint4 ca = a0, cb = b0;
-        a0 = a1;
-        b0 = b1;
-        if (c + 2 < nch) {
-          a1 = __ldg(ep + (c + 2) * 8);
-          b1 = __ldg(ep + (c + 2) * 8 + 1);
-        }
-        const uint32_t idx[4] = {ca.x, ca.z, cb.x, cb.z};
-        const uint32_t val[4] = {ca.y, ca.w, cb.y, cb.w};
-        typename VecT<C::VB>::T xv[4][C::VPL];
+      uint32_t idx[4], val[4];
+      if constexpr (C::E16) {
+        const uint32_t e4[4] = {cur[0].x, cur[0].y, cur[0].z, cur[0].w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int v = 0; v < C::VPL; ++v)
-            xv[q][v] = *reinterpret_cast<const typename VecT<C::VB>::T*>(
-                sbase + (size_t)idx[q] * C::PIXB + v * C::LPR * C::VB);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int v = 0; v < C::VPL; ++v) Fma<TX, C::EPV>::run(acc + v * C::EPV, xv[q][v], val[q]);
+        for (int q = 0; q < 4; ++q) { idx[q] = e4[q] & 0xffffu; val[q] = e4[q] >> 16; }
+      } else {
+        idx[0] = cur[0].x; val[0] = cur[0].y; idx[1] = cur[0].z; val[1] = cur[0].w;
+        idx[2] = cur[CW - 1].x; val[2] = cur[CW - 1].y; idx[3] = cur[CW - 1].z; val[3] = cur[CW - 1].w;
       }
+      typename VecT<C::VB>::T xv[4][C::VPL];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int v = 0; v < C::VPL; ++v)
+          xv[q][v] = *reinterpret_cast<const typename VecT<C::VB>::T*>(
+              sbase + (size_t)idx[q] * C::PIXB + v * C::LPR * C::VB);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int v = 0; v < C::VPL; ++v)
+          Fma<TX, C::EPV>::run(acc + v * C::EPV, xv[q][v], val[q]);
     }
     __syncthreads();
   }
