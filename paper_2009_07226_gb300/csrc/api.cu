@@ -139,6 +139,7 @@ struct PhaseTimer {
 struct CglsBufs {
   float *X, *R, *P, *Q, *Sv;
   uint16_t *h_pix, *h_ray;   // 16-bit staging copies of the product inputs
+  int* work;                 // work counter of the persistent product
   double *dpart, *gpart, *rpart, *log;
   uint32_t* max_x;
   CglsScalars sc;
@@ -162,7 +163,7 @@ xct_status enqueue_cgls(Plan& p, const float* yd, float* xd, int S, int st, int 
   if (x0) {
     XCT_TRY_CUDA(cudaMemsetAsync(B.max_x, 0, sizeof(uint32_t) * S_pad, s));
     XCT_TRY(to_internal(xd, B.X, p.pix_inv, npix, S, st, ntiles, B.max_x, s));
-    SpmmArgs a{&p.la, B.X, B.Q, st, ntiles, p.storage, k, B.max_x, nullptr, B.h_pix};
+    SpmmArgs a{&p.la, B.X, B.Q, st, ntiles, p.storage, k, B.max_x, nullptr, B.h_pix, B.work, p.err};
     XCT_TRY(spmm_timed(a, 0, tm, s));
     XCT_TRY_CUDA(cudaMemsetAsync(B.sc.max_r, 0, sizeof(uint32_t) * S_pad, s));
     XCT_TRY(cgls_residual(B.R, B.Q, nray, st, ntiles, B.sc.max_r, B.rpart, s));
@@ -171,26 +172,28 @@ xct_status enqueue_cgls(Plan& p, const float* yd, float* xd, int S, int st, int 
     XCT_TRY(cgls_residual(B.R, nullptr, nray, st, ntiles, B.sc.max_r, B.rpart, s));
   }
   XCT_TRY_CUDA(cudaMemsetAsync(B.P, 0, sizeof(float) * npix * S_pad, s));
+  const SpmmArgs probe_at{&p.lat, B.R, B.Sv, st, ntiles, p.storage, k, B.sc.max_r, B.gpart,
+                          B.h_ray, B.work, p.err};
+  const int nb_at = spmm_dot_count(probe_at);
   {
-    SpmmArgs a{&p.lat, B.R, B.Sv, st, ntiles, p.storage, k, B.sc.max_r, B.gpart, B.h_ray};
+    SpmmArgs a{&p.lat, B.R, B.Sv, st, ntiles, p.storage, k, B.sc.max_r, B.gpart, B.h_ray, B.work, p.err};
     XCT_TRY(spmm_timed(a, 1, tm, s));
   }
-  XCT_TRY(cgls_init_scalars(B.gpart, p.lat.nblocks, B.rpart, B.sc, B.log, S_pad, s));
+  XCT_TRY(cgls_init_scalars(B.gpart, nb_at, B.rpart, B.sc, B.log, S_pad, s));
   if (tm) XCT_TRY(tm->begin(2));
   XCT_TRY(cgls_update_p(B.P, B.Sv, npix, st, ntiles, B.sc, s));
   if (tm) XCT_TRY(tm->end(2));
   for (int it = 1; it <= iters; ++it) {
-    SpmmArgs ap{&p.la, B.P, B.Q, st, ntiles, p.storage, k, B.sc.max_p, B.dpart, B.h_pix};
+    SpmmArgs ap{&p.la, B.P, B.Q, st, ntiles, p.storage, k, B.sc.max_p, B.dpart, B.h_pix, B.work, p.err};
     XCT_TRY(spmm_timed(ap, 0, tm, s));
     if (tm) XCT_TRY(tm->begin(2));
-    XCT_TRY(cgls_alpha(B.dpart, p.la.nblocks, B.sc, S_pad, s));
+    XCT_TRY(cgls_alpha(B.dpart, spmm_dot_count(ap), B.sc, S_pad, s));
     XCT_TRY(cgls_update_xr(B.X, B.P, npix, B.R, B.Q, nray, st, ntiles, B.sc, B.rpart, s));
     if (tm) XCT_TRY(tm->end(2));
-    SpmmArgs at{&p.lat, B.R, B.Sv, st, ntiles, p.storage, k, B.sc.max_r, B.gpart, B.h_ray};
+    SpmmArgs at{&p.lat, B.R, B.Sv, st, ntiles, p.storage, k, B.sc.max_r, B.gpart, B.h_ray, B.work, p.err};
     XCT_TRY(spmm_timed(at, 1, tm, s));
     if (tm) XCT_TRY(tm->begin(2));
-    XCT_TRY(cgls_beta(B.gpart, p.lat.nblocks, B.rpart, B.sc, B.log + (size_t)it * S_pad * 2,
-                      S_pad, s));
+    XCT_TRY(cgls_beta(B.gpart, nb_at, B.rpart, B.sc, B.log + (size_t)it * S_pad * 2, S_pad, s));
     XCT_TRY(cgls_update_p(B.P, B.Sv, npix, st, ntiles, B.sc, s));
     if (tm) XCT_TRY(tm->end(2));
   }
@@ -239,8 +242,9 @@ xct_status cgls_impl(Plan& p, const float* y, float* x, int32_t S, int32_t iters
     XCT_TRY(ar.get(&B.h_pix, (size_t)p.npix * S_pad));
     XCT_TRY(ar.get(&B.h_ray, (size_t)p.nray * S_pad));
   }
-  XCT_TRY(ar.get(&B.dpart, (size_t)S_pad * std::max(p.la.nblocks, 1)));
-  XCT_TRY(ar.get(&B.gpart, (size_t)S_pad * std::max(p.lat.nblocks, 1)));
+  XCT_TRY(ar.get(&B.dpart, (size_t)S_pad * std::max(p.la.nblocks, 1) * kPipeConsumerWarps));
+  XCT_TRY(ar.get(&B.gpart, (size_t)S_pad * std::max(p.lat.nblocks, 1) * kPipeConsumerWarps));
+  XCT_TRY(ar.get(&B.work, 1));
   XCT_TRY(ar.get(&B.rpart, (size_t)S_pad * kVecBlocks));
   XCT_TRY(ar.get(&B.log, (size_t)(iters + 1) * S_pad * 2));
   XCT_TRY(ar.get(&B.max_x, (size_t)S_pad));
@@ -309,7 +313,14 @@ xct_status cgls_impl(Plan& p, const float* y, float* x, int32_t S, int32_t iters
   std::vector<int> act0((size_t)S_pad);
   XCT_TRY_CUDA(cudaMemcpyAsync(act0.data(), B.sc.active0, sizeof(int) * S_pad,
                                cudaMemcpyDeviceToHost, us));
+  int kerr = 0;
+  XCT_TRY_CUDA(cudaMemcpyAsync(&kerr, p.err, sizeof(int), cudaMemcpyDeviceToHost, us));
   XCT_TRY_CUDA(cudaStreamSynchronize(us));
+  if (kerr) {
+    XCT_TRY_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), us));
+    set_error("a bounded wait in the product kernel ran out; results are invalid");
+    return XCT_ERR_TIMEOUT;
+  }
   bool any = false;
   for (int i = 0; i < S; ++i) any = any || act0[i];
   if (!any) {
@@ -339,14 +350,23 @@ xct_status apply_impl(Plan& p, bool transposed, const float* in, float* out, int
   XCT_TRY(ar.get(&mx, (size_t)S_pad));
   uint16_t* h16 = nullptr;
   if (p.storage != XCT_F32) XCT_TRY(ar.get(&h16, (size_t)nin * S_pad));
+  int* work;
+  XCT_TRY(ar.get(&work, 1));
   XCT_TRY_CUDA(cudaMemsetAsync(mx, 0, sizeof(uint32_t) * S_pad, s));
   XCT_TRY(to_internal(iv.dev, Xi, in_inv, nin, S, st, ntiles, mx, s));
-  SpmmArgs a{&L, Xi, Yi, st, ntiles, p.storage, p.mat_scale_exp, mx, nullptr, h16};
+  SpmmArgs a{&L, Xi, Yi, st, ntiles, p.storage, p.mat_scale_exp, mx, nullptr, h16, work, p.err};
   XCT_TRY(spmm(a, s));
   XCT_TRY(to_natural(Yi, ov.dev, out_inv, nout, S, st, ntiles, s));
   if (ov.host) {
     XCT_TRY_CUDA(cudaMemcpyAsync(out, ov.dev, sizeof(float) * S * nout, cudaMemcpyDeviceToHost, s));
+    int kerr = 0;
+    XCT_TRY_CUDA(cudaMemcpyAsync(&kerr, p.err, sizeof(int), cudaMemcpyDeviceToHost, s));
     XCT_TRY_CUDA(cudaStreamSynchronize(s));
+    if (kerr) {
+      XCT_TRY_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), s));
+      set_error("a bounded wait in the product kernel ran out; results are invalid");
+      return XCT_ERR_TIMEOUT;
+    }
   }
   return XCT_OK;
 }

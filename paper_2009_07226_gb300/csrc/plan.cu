@@ -631,6 +631,15 @@ __global__ void seg_off_kernel(Seg* seg, const int64_t* off, int64_t n) {
   if (i < n) seg[i].off = off[i];
 }
 
+__global__ void stage_ent_kernel(const int64_t* slot_off, int64_t nstages, int64_t* stage_ent,
+                                 unsigned long long* emax) {
+  int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s > nstages) return;
+  stage_ent[s] = slot_off[s * kQuads];
+  if (s < nstages)
+    atomicMax(emax, (unsigned long long)(slot_off[(s + 1) * kQuads] - slot_off[s * kQuads]));
+}
+
 template <int EB>
 __global__ void pad_fill_kernel(void* ent, int64_t nslots, uint32_t zero_slot) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nslots;
@@ -744,7 +753,16 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
   }
   XCT_TRY_CUDA(cudaMemcpyAsync(&L.nslots, slot_off + L.nstages * kQuads, sizeof(int64_t),
                                cudaMemcpyDeviceToHost, s));
+  XCT_TRY(own.get(&L.stage_ent, L.nstages + 1));
+  unsigned long long* emax;
+  XCT_TRY(tmp.get(&emax, 1));
+  XCT_TRY_CUDA(cudaMemsetAsync(emax, 0, sizeof(unsigned long long), s));
+  stage_ent_kernel<<<grid_for(L.nstages + 1, 256), 256, 0, s>>>(slot_off, L.nstages, L.stage_ent, emax);
+  count_launch();
+  unsigned long long emax_h = 0;
+  XCT_TRY_CUDA(cudaMemcpyAsync(&emax_h, emax, sizeof(emax_h), cudaMemcpyDeviceToHost, s));
   XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  L.emax_slots = (int64_t)emax_h;
   if (L.ebytes == 8) {
     unsigned long long* e;
     XCT_TRY(own.get(&e, L.nslots));
@@ -769,7 +787,7 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
   XCT_TRY_CUDA(cudaGetLastError());
   XCT_TRY_CUDA(cudaStreamSynchronize(s));
   L.bytes = (int64_t)L.nslots * L.ebytes + L.nstages * (int64_t)sizeof(Seg) +
-            (L.nstages + 1) * 8 + (int64_t)(nb + 1) * 8 + total_fp * 4;
+            (L.nstages + 1) * 16 + (int64_t)(nb + 1) * 8 + total_fp * 4;
   own.move_to(keep);
   return XCT_OK;
 }
@@ -795,6 +813,8 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
   XCT_TRY(tmp.get(&cs_dev, 2 * (size_t)g.n_angles));
   XCT_TRY_CUDA(cudaMemcpyAsync(cs_dev, p.cs.data(), sizeof(double) * 2 * g.n_angles,
                                cudaMemcpyHostToDevice, s));
+  XCT_TRY(keep.get(&p.err, 1));
+  XCT_TRY_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), s));
   XCT_TRY(keep.get(&p.pix_order, p.npix));
   XCT_TRY(keep.get(&p.pix_inv, p.npix));
   XCT_TRY(keep.get(&p.ray_order, p.nray));
@@ -830,11 +850,29 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
   XCT_TRY(f64.get(&tval, p.nnz));
   XCT_TRY(transpose(rowptr, col, val, p.nray, p.npix, p.nnz, colptr, trow, tval, s));
 
-  const int32_t cap = kDefaultCapacity;
+  // Stage capacity: two pipeline buffers (128-byte staged rows plus the
+  // stage's packed entries) must fit in shared memory; a layout whose largest
+  // stage does not fit is rebuilt with a smaller capacity.
   CsrView ma{rowptr, col, val, p.nray, p.npix};
-  XCT_TRY(build_layout(ma, p.nnz, p.storage, cap, p.la, keep, s));
   CsrView mt{colptr, trow, tval, p.npix, p.nray};
-  XCT_TRY(build_layout(mt, p.nnz, p.storage, cap, p.lat, keep, s));
+  int32_t cap = p.storage == XCT_F32 ? 480 : 600;
+  for (int attempt = 0;; ++attempt) {
+    Arena la_mem(s), lat_mem(s);
+    Layout la, lat;
+    XCT_TRY(build_layout(ma, p.nnz, p.storage, cap, la, la_mem, s));
+    XCT_TRY(build_layout(mt, p.nnz, p.storage, cap, lat, lat_mem, s));
+    const bool fits = 2 * pipe_buffer_bytes(la, 128) <= kPipeSmemLimit &&
+                      2 * pipe_buffer_bytes(lat, 128) <= kPipeSmemLimit;
+    if (fits || attempt == 3 || cap <= 64) {
+      p.la = la;
+      p.lat = lat;
+      la_mem.move_to(keep);
+      lat_mem.move_to(keep);
+      break;
+    }
+    cap = cap * 3 / 4;
+  }
+  const int32_t cap_used = cap;
 
   if (p.flags & XCT_PLAN_KEEP_F64) {
     p.a_rowptr = rowptr; p.a_col = col; p.a_val = val;
@@ -853,7 +891,7 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
   st.nnz = p.nnz;
   st.storage = p.storage;
   st.rows_per_block = kRowsPerBlock;
-  st.stage_capacity = cap;
+  st.stage_capacity = cap_used;
   st.stages_a = p.la.nstages;
   st.stages_at = p.lat.nstages;
   st.slots_a = p.la.nslots;

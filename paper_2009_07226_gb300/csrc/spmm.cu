@@ -370,28 +370,28 @@ xct_status launch(const SpmmArgs& a, cudaStream_t s) {
   using C = Cfg<TX, ST>;
   const Layout& L = *a.L;
   const size_t smem = C::smem_bytes(L.cap);
-  static bool configured = false;  // attribute set once per instance
-  if (!configured) {
+  static int configured_for = -1;  // attribute set per shared-memory size
+  if (configured_for != (int)smem) {
     XCT_TRY_CUDA(cudaFuncSetAttribute(spmm_kernel<TX, ST>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = true;
+    configured_for = (int)smem;
   }
   if (L.nblocks == 0 || a.ntiles == 0) return XCT_OK;
-  const unsigned char* src = reinterpret_cast<const unsigned char*>(a.x);
-  if constexpr (C::E16) {
-    if (!a.staged16) {
-      set_error("16-bit storage needs a staging buffer");
-      return XCT_ERR_INVALID;
-    }
-    dim3 cgrid(152 * 4, (unsigned)a.ntiles);
-    to_staged16_kernel<TX, ST><<<cgrid, 256, 0, s>>>(a.x, a.staged16, L.ncols, a.in_max);
-    count_launch();
-    src = reinterpret_cast<const unsigned char*>(a.staged16);
-  }
+  const unsigned char* src = C::E16 ? reinterpret_cast<const unsigned char*>(a.staged16)
+                                    : reinterpret_cast<const unsigned char*>(a.x);
   dim3 grid((unsigned)L.nblocks, (unsigned)a.ntiles);
   spmm_kernel<TX, ST><<<grid, C::NT, smem, s>>>(L.blk_stage, L.stage_pix, L.pix, L.seg, L.ent,
                                                 L.nrows, L.ncols, L.cap, src, a.y, a.in_max,
                                                 a.mat_scale_exp, a.dot_partial);
+  count_launch();
+  XCT_TRY_CUDA(cudaGetLastError());
+  return XCT_OK;
+}
+
+template <class TX, int ST>
+xct_status launch_stage16(const SpmmArgs& a, cudaStream_t s) {
+  dim3 cgrid(152 * 4, (unsigned)a.ntiles);
+  to_staged16_kernel<TX, ST><<<cgrid, 256, 0, s>>>(a.x, a.staged16, a.L->ncols, a.in_max);
   count_launch();
   XCT_TRY_CUDA(cudaGetLastError());
   return XCT_OK;
@@ -407,6 +407,22 @@ xct_status dispatch(const SpmmArgs& a, cudaStream_t s) {
     case 16: return launch<TX, 16>(a, s);
     case 32: return launch<TX, 32>(a, s);
     case 64: return launch<TX, 64>(a, s);
+    default:
+      set_error("slices per tile %d not supported", a.st);
+      return XCT_ERR_UNSUPPORTED;
+  }
+}
+
+template <class TX>
+xct_status stage16(const SpmmArgs& a, cudaStream_t s) {
+  switch (a.st) {
+    case 1: return launch_stage16<TX, 1>(a, s);
+    case 2: return launch_stage16<TX, 2>(a, s);
+    case 4: return launch_stage16<TX, 4>(a, s);
+    case 8: return launch_stage16<TX, 8>(a, s);
+    case 16: return launch_stage16<TX, 16>(a, s);
+    case 32: return launch_stage16<TX, 32>(a, s);
+    case 64: return launch_stage16<TX, 64>(a, s);
     default:
       set_error("slices per tile %d not supported", a.st);
       return XCT_ERR_UNSUPPORTED;
@@ -432,13 +448,28 @@ xct_status spmm(const SpmmArgs& a, cudaStream_t s) {
     set_error("stage capacity %d exceeds the 16-bit index", a.L->cap);
     return XCT_ERR_UNSUPPORTED;
   }
+  if (a.storage != XCT_F32 && a.storage != XCT_F16 && a.storage != XCT_BF16) {
+    set_error("unknown storage type");
+    return XCT_ERR_INVALID;
+  }
+  if (a.storage != XCT_F32) {
+    if (!a.staged16) {
+      set_error("16-bit storage needs a staging buffer");
+      return XCT_ERR_INVALID;
+    }
+    if (a.L->ncols > 0 && a.ntiles > 0)
+      XCT_TRY(a.storage == XCT_F16 ? stage16<__half>(a, s) : stage16<__nv_bfloat16>(a, s));
+  }
+  if (spmm_pipe_applies(a)) return spmm_pipe(a, s);
   switch (a.storage) {
     case XCT_F32: return dispatch<float>(a, s);
     case XCT_F16: return dispatch<__half>(a, s);
-    case XCT_BF16: return dispatch<__nv_bfloat16>(a, s);
+    default: return dispatch<__nv_bfloat16>(a, s);
   }
-  set_error("unknown storage type");
-  return XCT_ERR_INVALID;
+}
+
+int spmm_dot_count(const SpmmArgs& a) {
+  return spmm_pipe_applies(a) ? a.L->nblocks * kPipeConsumerWarps : a.L->nblocks;
 }
 
 }  // namespace xct

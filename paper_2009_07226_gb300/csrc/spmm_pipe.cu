@@ -1,0 +1,450 @@
+// Persistent, warp-specialised form of the fused product Y = M X (paper
+// Sec. III-B: input buffering, register reuse, output buffering, multi-stage
+// buffering; Sec. III-C: mixed precision).
+//
+// One CTA per SM.  A producer warp takes blocks of 64 rows from a work
+// counter and streams each stage of each block into one of two shared-memory
+// buffers with bulk asynchronous copies (cp.async.bulk, completion counted in
+// bytes on an mbarrier): the block's staged input rows for the stage (one
+// 16..128-byte copy per row), the stage's packed entries and its segment
+// headers (one copy each).  Sixteen consumer warps compute from shared memory
+// only and release the buffer through a second mbarrier; while they work on
+// one stage the next one (possibly of the next block) is already in flight.
+// The lane layout of the consumers is the one of spmm.cu: a group of lanes
+// holds different slices of one row, so every shared-memory wavefront reads
+// one contiguous staged row.
+//
+// Every wait is bounded (about two seconds of wall time); a wait that runs out
+// sets the caller's error flag, waits (bounded) for the copies this CTA has in
+// flight and returns.
+#include "xct_internal.cuh"
+
+namespace xct {
+namespace {
+
+template <class TX> struct PBytes;
+template <> struct PBytes<float> { static constexpr int v = 4; };
+template <> struct PBytes<__half> { static constexpr int v = 2; };
+template <> struct PBytes<__nv_bfloat16> { static constexpr int v = 2; };
+
+template <class TX, int ST>
+struct PCfg {
+  static constexpr int XB = PBytes<TX>::v;
+  static constexpr int PIXB = ST * XB;
+  static constexpr int VB = 16;
+  static constexpr int LPR = PIXB >= 128 ? 8 : PIXB / 16;
+  static constexpr int VPL = PIXB / (VB * LPR);
+  static constexpr int EPV = VB / XB;
+  static constexpr int SPL = EPV * VPL;
+  static constexpr int RPW = 32 / LPR;
+  static constexpr int NC = kRowsPerBlock / RPW;   // consumer warps
+  static constexpr int NT = (NC + 1) * 32;         // + one producer warp
+  static constexpr bool E16 = XB == 2;
+  static constexpr int EB = E16 ? 4 : 8;           // bytes per packed entry
+};
+
+struct __align__(16) Hdr {
+  int32_t work;    // work item (tile * nblocks + block), -1 = no more work
+  int32_t kstage;  // stage index inside the block
+  int32_t last;    // last stage of the block
+  int32_t np;      // staged rows (0: a block without entries)
+};
+
+struct PipeArgs {
+  const int64_t* blk_stage;
+  const int64_t* stage_pix;
+  const int64_t* stage_ent;
+  const int32_t* pix;
+  const Seg* seg;
+  const unsigned char* ent;
+  int64_t nrows, ncols;
+  int cap, nblocks, ntiles;
+  const unsigned char* xs;   // staged rows [tile][ncols][PIXB bytes]
+  float* y;                  // [tile][nrows][ST]
+  const uint32_t* in_max;
+  int mat_scale_exp;
+  double* dot;               // [ntiles*ST][nblocks * NC] or null
+  int* work;
+  int* err;
+  uint32_t xbytes, ebytes;   // per-buffer region sizes (128-byte multiples)
+};
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t tx) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(tx)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase of `parity` to complete; false after ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = now_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 255u) == 0 && now_ns() - t0 > 2000000000ull) return false;
+  }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          su32(dst)),
+      "l"(src), "r"(bytes), "r"(su32(bar))
+      : "memory");
+}
+
+template <int VB> struct PVec;
+template <> struct PVec<16> { using T = uint4; };
+
+// mixed-precision FMA of one staged 16-byte vector (see spmm.cu)
+template <class TX, int EPV> struct PFma;
+template <int EPV> struct PFma<float, EPV> {
+  static __device__ __forceinline__ void run(float* acc, const uint4& v, uint32_t wbits) {
+    const float w = __uint_as_float(wbits);
+    const float* x = reinterpret_cast<const float*>(&v);
+#pragma unroll
+    for (int e = 0; e < EPV; ++e) acc[e] = fmaf(w, x[e], acc[e]);
+  }
+};
+template <int EPV> struct PFma<__half, EPV> {
+  static __device__ __forceinline__ void run(float* acc, const uint4& v, uint32_t wbits) {
+    const unsigned short w = (unsigned short)wbits;
+    const uint32_t* x = reinterpret_cast<const uint32_t*>(&v);
+#pragma unroll
+    for (int e = 0; e < EPV / 2; ++e)
+      asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+          "fma.rn.f32.f16 %0, lo, %3, %0;\n\tfma.rn.f32.f16 %1, hi, %3, %1;\n\t}"
+          : "+f"(acc[2 * e]), "+f"(acc[2 * e + 1])
+          : "r"(x[e]), "h"(w));
+  }
+};
+template <int EPV> struct PFma<__nv_bfloat16, EPV> {
+  static __device__ __forceinline__ void run(float* acc, const uint4& v, uint32_t wbits) {
+    const unsigned short w = (unsigned short)wbits;
+    const uint32_t* x = reinterpret_cast<const uint32_t*>(&v);
+#pragma unroll
+    for (int e = 0; e < EPV / 2; ++e)
+      asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+          "fma.rn.f32.bf16 %0, lo, %3, %0;\n\tfma.rn.f32.bf16 %1, hi, %3, %1;\n\t}"
+          : "+f"(acc[2 * e]), "+f"(acc[2 * e + 1])
+          : "r"(x[e]), "h"(w));
+  }
+};
+
+__device__ __forceinline__ int ceil_log2_exp_p(float m) {
+  if (!(m > 0.0f)) return 0;
+  int ex;
+  const float f = frexpf(m, &ex);
+  return f == 0.5f ? ex - 1 : ex;
+}
+
+template <class TX, int ST>
+__global__ void __launch_bounds__(PCfg<TX, ST>::NT, 1) spmm_pipe_kernel(PipeArgs a) {
+  using C = PCfg<TX, ST>;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const uint32_t bufbytes = a.xbytes + a.ebytes + 256 + 128;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * bufbytes);
+  uint64_t* empty = full + 2;
+  auto xbuf = [&](int b) { return smem + b * bufbytes; };
+  auto ebuf = [&](int b) { return smem + b * bufbytes + a.xbytes; };
+  auto sbuf = [&](int b) { return smem + b * bufbytes + a.xbytes + a.ebytes; };
+  auto hbuf = [&](int b) { return reinterpret_cast<Hdr*>(smem + b * bufbytes + a.xbytes + a.ebytes + 256); };
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], C::NC);
+    mbar_init(&empty[1], C::NC);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // zero slot (index cap) of both buffers: padding entries read 0.0 there
+  for (int i = tid; i < C::PIXB; i += C::NT) {
+    xbuf(0)[(size_t)a.cap * C::PIXB + i] = 0;
+    xbuf(1)[(size_t)a.cap * C::PIXB + i] = 0;
+  }
+  __syncthreads();
+
+  const int nwork = a.nblocks * a.ntiles;
+
+  if (warp == C::NC) {
+    // ----------------------------- producer -----------------------------
+    uint32_t it = 0;
+    bool ok = true;
+    int issued[2] = {-1, -1};  // last use of each buffer with copies in flight
+    while (ok) {
+      int w = 0;
+      if (lane == 0) w = atomicAdd(a.work, 1);
+      w = __shfl_sync(0xffffffffu, w, 0);
+      const bool done = w >= nwork;
+      const int tile = done ? 0 : w / a.nblocks, b = done ? 0 : w % a.nblocks;
+      const int64_t s0 = done ? 0 : a.blk_stage[b], s1 = done ? 0 : a.blk_stage[b + 1];
+      const int nst = done ? 1 : (s1 > s0 ? (int)(s1 - s0) : 1);
+      const unsigned char* xt = a.xs + (size_t)tile * a.ncols * C::PIXB;
+      for (int ks = 0; ks < nst && ok; ++ks, ++it) {
+        const int buf = it & 1;
+        const uint32_t use = it >> 1;
+        if (!mbar_wait(&empty[buf], (use & 1) ^ 1)) { ok = false; break; }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const bool real = !done && s1 > s0;
+        const int64_t s = s0 + ks;
+        const int64_t p0 = real ? a.stage_pix[s] : 0;
+        const int np = real ? (int)(a.stage_pix[s + 1] - p0) : 0;
+        const uint32_t eb = real ? (uint32_t)((a.stage_ent[s + 1] - a.stage_ent[s]) * C::EB) : 0u;
+        if (lane == 0) {
+          Hdr h;
+          h.work = done ? -1 : w;
+          h.kstage = ks;
+          h.last = (ks == nst - 1);
+          h.np = np;
+          *hbuf(buf) = h;
+          mbar_arrive_tx(&full[buf], (uint32_t)np * C::PIXB + eb + (real ? 256u : 0u));
+        }
+        __syncwarp();
+        if (real) {
+          issued[buf] = (int)use;
+          unsigned char* xd = xbuf(buf);
+          for (int p = lane; p < np; p += 32 * 8) {
+            int32_t gp[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) gp[j] = (p + 32 * j < np) ? __ldg(a.pix + p0 + p + 32 * j) : 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              if (p + 32 * j < np)
+                bulk_g2s(xd + (size_t)(p + 32 * j) * C::PIXB, xt + (size_t)gp[j] * C::PIXB, C::PIXB,
+                         &full[buf]);
+          }
+          if (lane == 0 && eb > 0)
+            bulk_g2s(ebuf(buf), a.ent + (size_t)a.stage_ent[s] * C::EB, eb, &full[buf]);
+          if (lane == 1) bulk_g2s(sbuf(buf), a.seg + s * kQuads, 256u, &full[buf]);
+        }
+      }
+      if (done) break;
+    }
+    if (!ok) {
+      if (lane == 0) atomicExch(a.err, 1);
+      // let copies already issued land before the CTA's shared memory goes away
+      for (int buf = 0; buf < 2; ++buf)
+        if (issued[buf] >= 0) mbar_wait(&full[buf], (uint32_t)issued[buf] & 1);
+    }
+    return;
+  }
+
+  // ------------------------------ consumers ------------------------------
+  const int rw = lane / C::LPR, sub = lane % C::LPR;
+  const int rb = warp * C::RPW + rw;
+  const int quad = rb >> 2, gq = rb & 3;
+  float acc[C::SPL];
+#pragma unroll
+  for (int i = 0; i < C::SPL; ++i) acc[i] = 0.0f;
+  for (uint32_t it = 0;; ++it) {
+    const int buf = it & 1;
+    if (!mbar_wait(&full[buf], (it >> 1) & 1)) {
+      if (lane == 0) atomicExch(a.err, 1);
+      return;
+    }
+    const Hdr h = *hbuf(buf);
+    if (h.work < 0) break;
+    if (h.kstage == 0) {
+#pragma unroll
+      for (int i = 0; i < C::SPL; ++i) acc[i] = 0.0f;
+    }
+    if (h.np > 0) {
+      const uint4 sgv = *reinterpret_cast<const uint4*>(sbuf(buf) + quad * 16);
+      const uint4 sg0 = *reinterpret_cast<const uint4*>(sbuf(buf));
+      const int64_t off = (int64_t)(((uint64_t)sgv.y << 32) | sgv.x);
+      const int64_t base = (int64_t)(((uint64_t)sg0.y << 32) | sg0.x);
+      const uint32_t cw = (gq < 2) ? sgv.z : sgv.w;
+      const int cnt = (int)((cw >> ((gq & 1) * 16)) & 0xffffu);
+      const int nch = (cnt + 3) >> 2;
+      const unsigned char* xs = xbuf(buf) + sub * C::VB;
+      if constexpr (C::E16) {
+        const uint4* ep = reinterpret_cast<const uint4*>(ebuf(buf) + (off - base) * 4) + gq;
+        uint4 nx = nch > 0 ? ep[0] : make_uint4(0, 0, 0, 0);
+        for (int c = 0; c < nch; ++c) {
+          const uint4 cur = nx;
+          if (c + 1 < nch) nx = ep[(c + 1) * 4];
+          const uint32_t e4[4] = {cur.x, cur.y, cur.z, cur.w};
+          uint4 xv[4][C::VPL];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int v = 0; v < C::VPL; ++v)
+              xv[q][v] = *reinterpret_cast<const uint4*>(xs + (size_t)(e4[q] & 0xffffu) * C::PIXB +
+                                                         v * C::LPR * C::VB);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int v = 0; v < C::VPL; ++v) PFma<TX, C::EPV>::run(acc + v * C::EPV, xv[q][v], e4[q] >> 16);
+        }
+      } else {
+        const uint4* ep = reinterpret_cast<const uint4*>(ebuf(buf) + (off - base) * 8) + gq * 2;
+        uint4 na = make_uint4(0, 0, 0, 0), nb = na;
+        if (nch > 0) { na = ep[0]; nb = ep[1]; }
+        for (int c = 0; c < nch; ++c) {
+          const uint4 ca = na, cb = nb;
+          if (c + 1 < nch) { na = ep[(c + 1) * 8]; nb = ep[(c + 1) * 8 + 1]; }
+          const uint32_t idx[4] = {ca.x, ca.z, cb.x, cb.z};
+          const uint32_t val[4] = {ca.y, ca.w, cb.y, cb.w};
+          uint4 xv[4][C::VPL];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int v = 0; v < C::VPL; ++v)
+              xv[q][v] = *reinterpret_cast<const uint4*>(xs + (size_t)idx[q] * C::PIXB + v * C::LPR * C::VB);
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int v = 0; v < C::VPL; ++v) PFma<TX, C::EPV>::run(acc + v * C::EPV, xv[q][v], val[q]);
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[buf]);
+    if (h.last) {
+      // ---- epilogue of a block: de-normalise, write, squared norms ----
+      const int tile = h.work / a.nblocks, b = h.work % a.nblocks;
+      const int64_t row = (int64_t)b * kRowsPerBlock + rb;
+      float* yt = a.y + (size_t)tile * a.nrows * ST;
+      float r[C::SPL];
+#pragma unroll
+      for (int v = 0; v < C::VPL; ++v)
+#pragma unroll
+        for (int e = 0; e < C::EPV; ++e) {
+          const int sl = v * C::LPR * C::EPV + sub * C::EPV + e;
+          float scale = 1.0f;
+          if (C::E16)
+            scale = ldexpf(1.0f, ceil_log2_exp_p(__uint_as_float(__ldg(a.in_max + tile * ST + sl))) -
+                                     a.mat_scale_exp);
+          r[v * C::EPV + e] = acc[v * C::EPV + e] * scale;
+        }
+      if (row < a.nrows) {
+#pragma unroll
+        for (int v = 0; v < C::VPL; ++v) {
+          float* dst = yt + (size_t)row * ST + v * C::LPR * C::EPV + sub * C::EPV;
+#pragma unroll
+          for (int q = 0; q < C::EPV / 4; ++q)
+            reinterpret_cast<float4*>(dst)[q] =
+                make_float4(r[v * C::EPV + 4 * q], r[v * C::EPV + 4 * q + 1],
+                            r[v * C::EPV + 4 * q + 2], r[v * C::EPV + 4 * q + 3]);
+        }
+      }
+      if (a.dot) {
+        double d[C::SPL];
+#pragma unroll
+        for (int i = 0; i < C::SPL; ++i) d[i] = (double)r[i] * (double)r[i];
+#pragma unroll
+        for (int o = C::LPR; o < 32; o <<= 1)
+#pragma unroll
+          for (int i = 0; i < C::SPL; ++i) d[i] += __shfl_xor_sync(0xffffffffu, d[i], o);
+        if (rw == 0) {
+          const size_t nb = (size_t)a.nblocks * C::NC;
+#pragma unroll
+          for (int v = 0; v < C::VPL; ++v)
+#pragma unroll
+            for (int e = 0; e < C::EPV; ++e) {
+              const int sl = v * C::LPR * C::EPV + sub * C::EPV + e;
+              a.dot[(size_t)(tile * ST + sl) * nb + (size_t)b * C::NC + warp] = d[v * C::EPV + e];
+            }
+        }
+      }
+    }
+  }
+}
+
+template <class TX, int ST>
+xct_status launch_pipe(const SpmmArgs& s, const unsigned char* src, cudaStream_t st) {
+  using C = PCfg<TX, ST>;
+  static_assert(C::NC == kPipeConsumerWarps, "dot partial layout assumes 16 consumer warps");
+  const Layout& L = *s.L;
+  PipeArgs a;
+  a.blk_stage = L.blk_stage;
+  a.stage_pix = L.stage_pix;
+  a.stage_ent = L.stage_ent;
+  a.pix = L.pix;
+  a.seg = L.seg;
+  a.ent = static_cast<const unsigned char*>(L.ent);
+  a.nrows = L.nrows;
+  a.ncols = L.ncols;
+  a.cap = L.cap;
+  a.nblocks = L.nblocks;
+  a.ntiles = s.ntiles;
+  a.xs = src;
+  a.y = s.y;
+  a.in_max = s.in_max;
+  a.mat_scale_exp = s.mat_scale_exp;
+  a.dot = s.dot_partial;
+  a.work = s.work;
+  a.err = s.err;
+  a.xbytes = (uint32_t)(((size_t)(L.cap + 1) * C::PIXB + 127) / 128 * 128);
+  a.ebytes = (uint32_t)(((size_t)L.emax_slots * C::EB + 127) / 128 * 128);
+  const size_t smem = 2 * ((size_t)a.xbytes + a.ebytes + 256 + 128) + 64;
+  static int configured_for = -1;
+  if (configured_for != (int)smem) {
+    XCT_TRY_CUDA(cudaFuncSetAttribute(spmm_pipe_kernel<TX, ST>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    configured_for = (int)smem;
+  }
+  int dev = 0, sms = 0;
+  XCT_TRY_CUDA(cudaGetDevice(&dev));
+  XCT_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int nwork = L.nblocks * s.ntiles;
+  const int grid = nwork < sms ? nwork : sms;
+  XCT_TRY_CUDA(cudaMemsetAsync(s.work, 0, sizeof(int), st));
+  spmm_pipe_kernel<TX, ST><<<grid, C::NT, smem, st>>>(a);
+  count_launch();
+  XCT_TRY_CUDA(cudaGetLastError());
+  return XCT_OK;
+}
+
+template <class TX>
+xct_status dispatch_pipe(const SpmmArgs& s, const unsigned char* src, cudaStream_t st) {
+  // the persistent form is built for 128-byte staged rows only
+  constexpr int kST = 128 / PBytes<TX>::v;
+  if (s.st != kST) {
+    set_error("persistent product: unsupported tile width %d", s.st);
+    return XCT_ERR_UNSUPPORTED;
+  }
+  return launch_pipe<TX, kST>(s, src, st);
+}
+
+}  // namespace
+
+// The persistent form needs 16-byte lane vectors and 128-byte staged rows
+// (64 slices in 16 bits, 32 in FP32) and two buffers in shared memory.
+bool spmm_pipe_applies(const SpmmArgs& a) {
+  const int pixb = a.st * (a.storage == XCT_F32 ? 4 : 2);
+  if (pixb != 128 || !a.work || !a.err) return false;
+  if (a.L->nblocks == 0) return false;
+  return 2 * pipe_buffer_bytes(*a.L, 128) <= kPipeSmemLimit;
+}
+
+xct_status spmm_pipe(const SpmmArgs& a, cudaStream_t s) {
+  const unsigned char* src = reinterpret_cast<const unsigned char*>(a.x);
+  if (a.storage == XCT_F32) return dispatch_pipe<float>(a, src, s);
+  if (a.storage == XCT_F16) return dispatch_pipe<__half>(a, reinterpret_cast<const unsigned char*>(a.staged16), s);
+  return dispatch_pipe<__nv_bfloat16>(a, reinterpret_cast<const unsigned char*>(a.staged16), s);
+}
+
+}  // namespace xct

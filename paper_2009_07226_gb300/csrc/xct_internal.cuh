@@ -100,8 +100,19 @@ struct Layout {
   int32_t* pix = nullptr;         // staged input row ids, stage by stage
   Seg* seg = nullptr;             // [nstages * kQuads]
   void* ent = nullptr;            // packed entries
+  int64_t* stage_ent = nullptr;   // [nstages + 1] first slot of each stage's entries
+  int64_t emax_slots = 0;         // largest stage, in slots
   int64_t bytes = 0;
 };
+
+// Shared memory of one pipeline buffer (staged rows of `pixb` bytes, the
+// stage's packed entries, its segment headers) -- see spmm_pipe.cu.
+inline size_t pipe_buffer_bytes(const Layout& L, int pixb) {
+  size_t x = ((size_t)(L.cap + 1) * pixb + 127) / 128 * 128;
+  size_t e = ((size_t)L.emax_slots * L.ebytes + 127) / 128 * 128;
+  return x + e + 128 * 2 + 256;
+}
+constexpr size_t kPipeSmemLimit = 225 * 1024;
 
 struct Plan {
   xct_geometry g{};
@@ -116,6 +127,7 @@ struct Plan {
   int32_t* ray_inv = nullptr;
   Layout la, lat;
   int32_t mat_scale_exp = 0;     // k: stored value = RN(l * 2^k)
+  int* err = nullptr;            // device flag: a bounded wait in a kernel ran out
   // kept FP64 matrices (ordered ids), only with XCT_PLAN_KEEP_F64
   int64_t* a_rowptr = nullptr; int32_t* a_col = nullptr; double* a_val = nullptr;
   int64_t* t_rowptr = nullptr; int32_t* t_col = nullptr; double* t_val = nullptr;
@@ -148,8 +160,17 @@ struct SpmmArgs {
   double* dot_partial;     // nullable: [ntiles*st][nblocks] sum of y^2 per block
   uint16_t* staged16;      // 16-bit storage: scratch [ntiles][L->ncols][st] for the
                            // normalised 16-bit copy of x (unused for FP32)
+  int* work;               // scratch: one work counter (persistent form)
+  int* err;                // device flag set to 1 if a bounded wait ran out
 };
 xct_status spmm(const SpmmArgs& a, cudaStream_t s);
+// the persistent warp-specialised form (spmm_pipe.cu); false if it does not
+// apply to this layout / tile width (the caller then uses the staged form)
+bool spmm_pipe_applies(const SpmmArgs& a);
+xct_status spmm_pipe(const SpmmArgs& a, cudaStream_t s);
+constexpr int kPipeConsumerWarps = 16;
+// number of per-slice partial sums spmm() writes for dot_partial (per slice)
+int spmm_dot_count(const SpmmArgs& a);
 bool spmm_supported(xct_dtype storage, int st);
 int pick_slices_per_tile(xct_dtype storage, int S);
 
