@@ -570,6 +570,12 @@ __global__ void __launch_bounds__(kFpThreads) fp_fill_kernel(CsrView m, const in
   (void)red;
 }
 
+// footprint lists start on 16-byte boundaries: sizes rounded up to 4 ids
+__global__ void round4_kernel(const int64_t* in, int32_t n, int64_t* out) {
+  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b < n) out[b] = (in[b] + 3) & ~(int64_t)3;
+}
+
 __global__ void stage_count_kernel(const int64_t* fp_size, int32_t nblocks, int32_t cap,
                                    int64_t* nst) {
   int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -701,9 +707,10 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
   L.nblocks = (int32_t)((m.nrows + kRowsPerBlock - 1) / kRowsPerBlock);
   const int32_t nb = L.nblocks;
   Arena tmp(s);
-  int64_t *fp_size, *fp_off, *nst;
+  int64_t *fp_size, *fp_pad, *fp_off, *nst;
   int32_t* epos;
   XCT_TRY(tmp.get(&fp_size, nb));
+  XCT_TRY(tmp.get(&fp_pad, nb));
   XCT_TRY(tmp.get(&fp_off, nb + 1));
   XCT_TRY(tmp.get(&nst, nb));
   XCT_TRY(tmp.get(&epos, nnz));
@@ -717,13 +724,18 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
     fp_count_kernel<<<nb, kFpThreads, bm_smem, s>>>(m, fp_size);
     count_launch();
   }
-  XCT_TRY(exclusive_scan_i64(fp_size, fp_off, nb, s));
+  if (nb > 0) {
+    round4_kernel<<<grid_for(nb, 256), 256, 0, s>>>(fp_size, nb, fp_pad);
+    count_launch();
+  }
+  XCT_TRY(exclusive_scan_i64(fp_pad, fp_off, nb, s));
   int64_t total_fp = 0;
   XCT_TRY_CUDA(cudaMemcpyAsync(&total_fp, fp_off + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   XCT_TRY_CUDA(cudaStreamSynchronize(s));
   L.footprint = total_fp;
   Arena own(s);
-  XCT_TRY(own.get(&L.pix, total_fp));
+  XCT_TRY(own.get(&L.pix, total_fp + 4));   // padded lists, +4 for rounded copies
+  XCT_TRY_CUDA(cudaMemsetAsync(L.pix, 0, sizeof(int32_t) * (total_fp + 4), s));
   XCT_TRY(own.get(&L.blk_stage, nb + 1));
   if (nb > 0) {
     fp_fill_kernel<<<nb, kFpThreads, fill_smem, s>>>(m, fp_off, L.pix, epos);
@@ -870,7 +882,7 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
       lat_mem.move_to(keep);
       break;
     }
-    cap = cap * 3 / 4;
+    cap = (cap * 3 / 4) & ~3;   // multiple of 4: stage lists stay 16-byte aligned
   }
   const int32_t cap_used = cap;
 

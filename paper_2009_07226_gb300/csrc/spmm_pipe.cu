@@ -114,8 +114,13 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-template <int VB> struct PVec;
-template <> struct PVec<16> { using T = uint4; };
+__device__ __forceinline__ void cp16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+// arrive on `bar` once every cp.async this thread issued so far has landed
+__device__ __forceinline__ void cp_arrive_noinc(uint64_t* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(bar)) : "memory");
+}
 
 // mixed-precision FMA of one staged 16-byte vector (see spmm.cu)
 template <class TX, int EPV> struct PFma;
@@ -164,8 +169,12 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, 1) spmm_pipe_kernel(PipeArgs
   using C = PCfg<TX, ST>;
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t bufbytes = a.xbytes + a.ebytes + 256 + 128;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * bufbytes);
+  const uint32_t listbytes = (uint32_t)(((size_t)a.cap * 4 + 127) / 128 * 128);
+  int32_t* lists = reinterpret_cast<int32_t*>(smem + 2 * bufbytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * bufbytes + 2 * listbytes);
   uint64_t* empty = full + 2;
+  uint64_t* plbar = full + 4;   // row-id list of a stage landed
+  auto plist = [&](int slot) { return lists + (size_t)slot * (listbytes / 4); };
   auto xbuf = [&](int b) { return smem + b * bufbytes; };
   auto ebuf = [&](int b) { return smem + b * bufbytes + a.xbytes; };
   auto sbuf = [&](int b) { return smem + b * bufbytes + a.xbytes + a.ebytes; };
@@ -173,10 +182,12 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, 1) spmm_pipe_kernel(PipeArgs
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    mbar_init(&full[0], 1);
-    mbar_init(&full[1], 1);
+    mbar_init(&full[0], 33);
+    mbar_init(&full[1], 33);
     mbar_init(&empty[0], C::NC);
     mbar_init(&empty[1], C::NC);
+    mbar_init(&plbar[0], 1);
+    mbar_init(&plbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // zero slot (index cap) of both buffers: padding entries read 0.0 there
@@ -190,57 +201,94 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, 1) spmm_pipe_kernel(PipeArgs
 
   if (warp == C::NC) {
     // ----------------------------- producer -----------------------------
-    uint32_t it = 0;
-    bool ok = true;
-    int issued[2] = {-1, -1};  // last use of each buffer with copies in flight
-    while (ok) {
+    // A stage reference: work item, stage index in its block, stages in the
+    // block, layout stage (-1 for a block without entries); w = -1: no more.
+    struct Ref { int w, k, nst; int64_t s; };
+    auto fetch = [&]() -> Ref {
       int w = 0;
       if (lane == 0) w = atomicAdd(a.work, 1);
       w = __shfl_sync(0xffffffffu, w, 0);
-      const bool done = w >= nwork;
-      const int tile = done ? 0 : w / a.nblocks, b = done ? 0 : w % a.nblocks;
-      const int64_t s0 = done ? 0 : a.blk_stage[b], s1 = done ? 0 : a.blk_stage[b + 1];
-      const int nst = done ? 1 : (s1 > s0 ? (int)(s1 - s0) : 1);
-      const unsigned char* xt = a.xs + (size_t)tile * a.ncols * C::PIXB;
-      for (int ks = 0; ks < nst && ok; ++ks, ++it) {
-        const int buf = it & 1;
-        const uint32_t use = it >> 1;
-        if (!mbar_wait(&empty[buf], (use & 1) ^ 1)) { ok = false; break; }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const bool real = !done && s1 > s0;
-        const int64_t s = s0 + ks;
-        const int64_t p0 = real ? a.stage_pix[s] : 0;
-        const int np = real ? (int)(a.stage_pix[s + 1] - p0) : 0;
-        const uint32_t eb = real ? (uint32_t)((a.stage_ent[s + 1] - a.stage_ent[s]) * C::EB) : 0u;
-        if (lane == 0) {
-          Hdr h;
-          h.work = done ? -1 : w;
-          h.kstage = ks;
-          h.last = (ks == nst - 1);
-          h.np = np;
-          *hbuf(buf) = h;
-          mbar_arrive_tx(&full[buf], (uint32_t)np * C::PIXB + eb + (real ? 256u : 0u));
-        }
-        __syncwarp();
-        if (real) {
-          issued[buf] = (int)use;
-          unsigned char* xd = xbuf(buf);
-          for (int p = lane; p < np; p += 32 * 8) {
-            int32_t gp[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) gp[j] = (p + 32 * j < np) ? __ldg(a.pix + p0 + p + 32 * j) : 0;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              if (p + 32 * j < np)
-                bulk_g2s(xd + (size_t)(p + 32 * j) * C::PIXB, xt + (size_t)gp[j] * C::PIXB, C::PIXB,
-                         &full[buf]);
-          }
-          if (lane == 0 && eb > 0)
-            bulk_g2s(ebuf(buf), a.ent + (size_t)a.stage_ent[s] * C::EB, eb, &full[buf]);
-          if (lane == 1) bulk_g2s(sbuf(buf), a.seg + s * kQuads, 256u, &full[buf]);
-        }
+      if (w >= nwork) return Ref{-1, 0, 1, -1};
+      const int b = w % a.nblocks;
+      const int64_t s0 = a.blk_stage[b], s1 = a.blk_stage[b + 1];
+      return Ref{w, 0, s1 > s0 ? (int)(s1 - s0) : 1, s1 > s0 ? s0 : (int64_t)-1};
+    };
+    // the row-id list of stage r into list slot `slot` (one bulk copy; the
+    // lists are 16-byte aligned and padded to 4 ids)
+    auto request = [&](const Ref& r, int slot) {
+      if (lane != 0) return;
+      if (r.w >= 0 && r.s >= 0) {
+        const int64_t p0 = a.stage_pix[r.s];
+        const uint32_t n4 = (uint32_t)(((a.stage_pix[r.s + 1] - p0) + 3) & ~(int64_t)3);
+        mbar_arrive_tx(&plbar[slot], n4 * 4u);
+        bulk_g2s(plist(slot), a.pix + p0, n4 * 4u, &plbar[slot]);
+      } else {
+        mbar_arrive(&plbar[slot]);
       }
-      if (done) break;
+    };
+    bool ok = true;
+    int issued[2] = {-1, -1};  // last use of each buffer with copies in flight
+    Ref cur = fetch();
+    request(cur, 0);
+    for (uint32_t it = 0;; ++it) {
+      const int buf = it & 1;
+      const uint32_t use = it >> 1;
+      Ref nxt{-1, 0, 1, -1};
+      if (cur.w >= 0) {
+        nxt = (cur.k + 1 < cur.nst) ? Ref{cur.w, cur.k + 1, cur.nst, cur.s >= 0 ? cur.s + 1 : -1} : fetch();
+        // this warp's reads of list slot buf^1 (stage it-1) precede the copy into it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        request(nxt, buf ^ 1);
+      }
+      if (!mbar_wait(&empty[buf], (use & 1) ^ 1)) { ok = false; break; }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const bool real = cur.w >= 0 && cur.s >= 0;
+      if (real && !mbar_wait(&plbar[buf], use & 1)) { ok = false; break; }
+      const int tile = cur.w >= 0 ? cur.w / a.nblocks : 0;
+      const unsigned char* xt = a.xs + (size_t)tile * a.ncols * C::PIXB;
+      const int64_t p0 = real ? a.stage_pix[cur.s] : 0;
+      const int np = real ? (int)(a.stage_pix[cur.s + 1] - p0) : 0;
+      const uint32_t eb = real ? (uint32_t)((a.stage_ent[cur.s + 1] - a.stage_ent[cur.s]) * C::EB) : 0u;
+      if (lane == 0) {
+        Hdr h;
+        h.work = cur.w;
+        h.kstage = cur.k;
+        h.last = (cur.k == cur.nst - 1);
+        h.np = np;
+        *hbuf(buf) = h;
+      }
+      if (real) {
+        issued[buf] = (int)use;
+        // staged rows: 16-byte pieces, PPR lanes per row, RPI rows per instruction
+        constexpr int PPR = C::PIXB / 16;
+        constexpr int RPI = 32 / PPR;
+        unsigned char* xd = xbuf(buf);
+        const int32_t* pl = plist(buf);
+        const int pr = lane / PPR, pc = lane % PPR;
+        for (int r0 = 0; r0 < np; r0 += RPI * 8) {
+          int32_t gp[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int r = r0 + j * RPI + pr;
+            gp[j] = r < np ? pl[r] : 0;
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int r = r0 + j * RPI + pr;
+            if (r < np) cp16(xd + (size_t)r * C::PIXB + pc * 16, xt + (size_t)gp[j] * C::PIXB + pc * 16);
+          }
+        }
+        // the stage's packed entries and its segment headers
+        const unsigned char* es = a.ent + (size_t)a.stage_ent[cur.s] * C::EB;
+        unsigned char* ed = ebuf(buf);
+        for (uint32_t o = (uint32_t)lane * 16u; o < eb; o += 32u * 16u) cp16(ed + o, es + o);
+        if (lane < 16)
+          cp16(sbuf(buf) + lane * 16, reinterpret_cast<const unsigned char*>(a.seg + cur.s * kQuads) + lane * 16);
+      }
+      cp_arrive_noinc(&full[buf]);
+      if (lane == 0) mbar_arrive(&full[buf]);   // publishes the header
+      if (cur.w < 0) break;
+      cur = nxt;
     }
     if (!ok) {
       if (lane == 0) atomicExch(a.err, 1);
@@ -399,7 +447,8 @@ xct_status launch_pipe(const SpmmArgs& s, const unsigned char* src, cudaStream_t
   a.err = s.err;
   a.xbytes = (uint32_t)(((size_t)(L.cap + 1) * C::PIXB + 127) / 128 * 128);
   a.ebytes = (uint32_t)(((size_t)L.emax_slots * C::EB + 127) / 128 * 128);
-  const size_t smem = 2 * ((size_t)a.xbytes + a.ebytes + 256 + 128) + 64;
+  const size_t listbytes = ((size_t)L.cap * 4 + 127) / 128 * 128;
+  const size_t smem = 2 * ((size_t)a.xbytes + a.ebytes + 256 + 128) + 2 * listbytes + 64;
   static int configured_for = -1;
   if (configured_for != (int)smem) {
     XCT_TRY_CUDA(cudaFuncSetAttribute(spmm_pipe_kernel<TX, ST>,

@@ -110,7 +110,8 @@ struct Layout {
 inline size_t pipe_buffer_bytes(const Layout& L, int pixb) {
   size_t x = ((size_t)(L.cap + 1) * pixb + 127) / 128 * 128;
   size_t e = ((size_t)L.emax_slots * L.ebytes + 127) / 128 * 128;
-  return x + e + 128 * 2 + 256;
+  size_t list = ((size_t)L.cap * 4 + 127) / 128 * 128;
+  return x + e + list + 128 * 2 + 256;
 }
 constexpr size_t kPipeSmemLimit = 225 * 1024;
 
