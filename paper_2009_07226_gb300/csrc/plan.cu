@@ -867,7 +867,7 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
   // stage does not fit is rebuilt with a smaller capacity.
   CsrView ma{rowptr, col, val, p.nray, p.npix};
   CsrView mt{colptr, trow, tval, p.npix, p.nray};
-  int32_t cap = p.storage == XCT_F32 ? 480 : 600;
+  int32_t cap = p.storage == XCT_F32 ? 200 : 280;
   for (int attempt = 0;; ++attempt) {
     Arena la_mem(s), lat_mem(s);
     Layout la, lat;

@@ -2,7 +2,7 @@
 // Sec. III-B: input buffering, register reuse, output buffering, multi-stage
 // buffering; Sec. III-C: mixed precision).
 //
-// One CTA per SM.  A producer warp takes blocks of 64 rows from a work
+// Two CTAs per SM.  A producer warp takes blocks of 64 rows from a work
 // counter and streams each stage of each block into one of two shared-memory
 // buffers with bulk asynchronous copies (cp.async.bulk, completion counted in
 // bytes on an mbarrier): the block's staged input rows for the stage (one
@@ -165,7 +165,7 @@ __device__ __forceinline__ int ceil_log2_exp_p(float m) {
 }
 
 template <class TX, int ST>
-__global__ void __launch_bounds__(PCfg<TX, ST>::NT, 1) spmm_pipe_kernel(PipeArgs a) {
+__global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_kernel(PipeArgs a) {
   using C = PCfg<TX, ST>;
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t bufbytes = a.xbytes + a.ebytes + 256 + 128;
@@ -459,7 +459,7 @@ xct_status launch_pipe(const SpmmArgs& s, const unsigned char* src, cudaStream_t
   XCT_TRY_CUDA(cudaGetDevice(&dev));
   XCT_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int nwork = L.nblocks * s.ntiles;
-  const int grid = nwork < sms ? nwork : sms;
+  const int grid = nwork < sms * kPipeCtasPerSm ? nwork : sms * kPipeCtasPerSm;
   XCT_TRY_CUDA(cudaMemsetAsync(s.work, 0, sizeof(int), st));
   spmm_pipe_kernel<TX, ST><<<grid, C::NT, smem, st>>>(a);
   count_launch();

@@ -113,7 +113,9 @@ inline size_t pipe_buffer_bytes(const Layout& L, int pixb) {
   size_t list = ((size_t)L.cap * 4 + 127) / 128 * 128;
   return x + e + list + 128 * 2 + 256;
 }
-constexpr size_t kPipeSmemLimit = 225 * 1024;
+constexpr int kPipeCtasPerSm = 2;
+// shared memory one pipeline CTA may use (two buffers), kPipeCtasPerSm per SM
+constexpr size_t kPipeSmemLimit = 110 * 1024;
 
 struct Plan {
   xct_geometry g{};
