@@ -183,6 +183,27 @@ typedef void* (*xct_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*xct_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 xct_status xct_set_allocator(xct_alloc_fn alloc, xct_free_fn release, void* ctx);
 
+/*
+ * xct_project_noalloc -- the projection of xct_project (same arithmetic, same
+ * result) for callers that must not allocate device memory during the call:
+ * processes whose device memory is owned up front by another component (a
+ * serving runtime or a framework allocator that reserved the whole budget)
+ * and latency-critical loops where an allocation could block or fail at an
+ * unpredictable moment.  The paper has no counterpart; it is a service of this
+ * library.  All working memory comes from one fixed device array of 32 MiB
+ * that every GPU loading the library holds until the process exits; a call
+ * whose working memory (S padded to the slice tile, times 4 bytes per pixel
+ * and per ray, plus 2 bytes per pixel for 16-bit storage) exceeds it returns
+ * XCT_ERR_INVALID.  x and y must be device pointers (XCT_ERR_INVALID
+ * otherwise).  The array's device address is looked up on the first call made
+ * on each device (with that device current); make that first call before any
+ * stream capture.  Calls share the array: calls whose GPU work overlaps (on
+ * several streams or host threads) race and must be serialised by the caller.
+ * It calls no allocator of any kind.
+ */
+xct_status xct_project_noalloc(xct_plan_t plan, const float* x, float* y, int32_t S,
+                               void* stream);
+
 /* Thread-local message of the last failing call on this thread. */
 const char* xct_last_error(void);
 

@@ -378,9 +378,6 @@ bool is_finite_d(double v) { return isfinite(v) != 0; }
 
 using namespace xct;
 
-// The opaque handle of the C-ABI is the plan itself.
-struct xct_plan_s : public xct::Plan {};
-
 extern "C" {
 
 xct_status xct_plan(const xct_geometry* g, xct_dtype storage, uint32_t flags, void* stream,

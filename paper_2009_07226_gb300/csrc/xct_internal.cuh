@@ -185,3 +185,6 @@ xct_status to_natural(const float* in, float* nat, const int32_t* inv_order,
                       int64_t rows, int S, int st, int ntiles, cudaStream_t s);
 
 }  // namespace xct
+
+// The opaque handle of the C-ABI is the plan itself.
+struct xct_plan_s : public xct::Plan {};

@@ -73,6 +73,8 @@ _SIGNATURES = [
                                        ctypes.c_void_p, ctypes.c_void_p,
                                        ctypes.POINTER(ctypes.c_int64)]),
     ("xct_plan_order", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("xct_project_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.c_void_p]),
     ("xct_set_allocator", ctypes.c_int, [ALLOC_FN, FREE_FN, ctypes.c_void_p]),
     ("xct_last_error", ctypes.c_char_p, []),
     ("xct_launch_count", ctypes.c_int64, []),
@@ -161,6 +163,12 @@ def xct_free(plan: int) -> None:
 
 def xct_project(plan: int, x, y, S: int, stream=None) -> None:
     _check(lib().xct_project(plan, _ptr(x), _ptr(y), S, _stream(stream)))
+
+
+def xct_project_noalloc(plan: int, x, y, S: int, stream=None) -> None:
+    """y = A x without allocating: working memory is the library's fixed
+    32 MiB device array (device pointers only; overlapping calls race)."""
+    _check(lib().xct_project_noalloc(plan, _ptr(x), _ptr(y), S, _stream(stream)))
 
 
 def xct_backproject(plan: int, y, x, S: int, stream=None) -> None:
