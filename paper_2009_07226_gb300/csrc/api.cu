@@ -145,9 +145,14 @@ struct CglsBufs {
   CglsScalars sc;
 };
 
+// the staging pre-pass counts as vector work (kind 2), the product kernel as
+// projection (0) or back projection (1)
 xct_status spmm_timed(const SpmmArgs& a, int kind, PhaseTimer* tm, cudaStream_t s) {
+  if (tm) XCT_TRY(tm->begin(2));
+  XCT_TRY(spmm_stage(a, s));
+  if (tm) XCT_TRY(tm->end(2));
   if (tm) XCT_TRY(tm->begin(kind));
-  XCT_TRY(spmm(a, s));
+  XCT_TRY(spmm_run(a, s));
   if (tm) XCT_TRY(tm->end(kind));
   return XCT_OK;
 }

@@ -443,7 +443,17 @@ int pick_slices_per_tile(xct_dtype storage, int S) {
   return st;
 }
 
-xct_status spmm(const SpmmArgs& a, cudaStream_t s) {
+xct_status spmm_stage(const SpmmArgs& a, cudaStream_t s) {
+  if (a.storage == XCT_F32) return XCT_OK;
+  if (!a.staged16) {
+    set_error("16-bit storage needs a staging buffer");
+    return XCT_ERR_INVALID;
+  }
+  if (a.L->ncols == 0 || a.ntiles == 0) return XCT_OK;
+  return a.storage == XCT_F16 ? stage16<__half>(a, s) : stage16<__nv_bfloat16>(a, s);
+}
+
+xct_status spmm_run(const SpmmArgs& a, cudaStream_t s) {
   if (a.L->cap > 65535) {
     set_error("stage capacity %d exceeds the 16-bit index", a.L->cap);
     return XCT_ERR_UNSUPPORTED;
@@ -452,20 +462,17 @@ xct_status spmm(const SpmmArgs& a, cudaStream_t s) {
     set_error("unknown storage type");
     return XCT_ERR_INVALID;
   }
-  if (a.storage != XCT_F32) {
-    if (!a.staged16) {
-      set_error("16-bit storage needs a staging buffer");
-      return XCT_ERR_INVALID;
-    }
-    if (a.L->ncols > 0 && a.ntiles > 0)
-      XCT_TRY(a.storage == XCT_F16 ? stage16<__half>(a, s) : stage16<__nv_bfloat16>(a, s));
-  }
   if (spmm_pipe_applies(a)) return spmm_pipe(a, s);
   switch (a.storage) {
     case XCT_F32: return dispatch<float>(a, s);
     case XCT_F16: return dispatch<__half>(a, s);
     default: return dispatch<__nv_bfloat16>(a, s);
   }
+}
+
+xct_status spmm(const SpmmArgs& a, cudaStream_t s) {
+  XCT_TRY(spmm_stage(a, s));
+  return spmm_run(a, s);
 }
 
 int spmm_dot_count(const SpmmArgs& a) {

@@ -166,7 +166,11 @@ struct SpmmArgs {
   int* work;               // scratch: one work counter (persistent form)
   int* err;                // device flag set to 1 if a bounded wait ran out
 };
-xct_status spmm(const SpmmArgs& a, cudaStream_t s);
+xct_status spmm(const SpmmArgs& a, cudaStream_t s);   // = spmm_stage + spmm_run
+// 16-bit storage: the normalised 16-bit copy of the input (no-op for FP32)
+xct_status spmm_stage(const SpmmArgs& a, cudaStream_t s);
+// the product kernel itself
+xct_status spmm_run(const SpmmArgs& a, cudaStream_t s);
 // the persistent warp-specialised form (spmm_pipe.cu); false if it does not
 // apply to this layout / tile width (the caller then uses the staged form)
 bool spmm_pipe_applies(const SpmmArgs& a);
