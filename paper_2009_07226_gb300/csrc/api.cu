@@ -247,8 +247,8 @@ xct_status cgls_impl(Plan& p, const float* y, float* x, int32_t S, int32_t iters
     XCT_TRY(ar.get(&B.h_pix, (size_t)p.npix * S_pad));
     XCT_TRY(ar.get(&B.h_ray, (size_t)p.nray * S_pad));
   }
-  XCT_TRY(ar.get(&B.dpart, (size_t)S_pad * std::max(p.la.nblocks, 1) * kPipeConsumerWarps));
-  XCT_TRY(ar.get(&B.gpart, (size_t)S_pad * std::max(p.lat.nblocks, 1) * kPipeConsumerWarps));
+  XCT_TRY(ar.get(&B.dpart, (size_t)S_pad * std::max(p.la.nblocks, 1)));
+  XCT_TRY(ar.get(&B.gpart, (size_t)S_pad * std::max(p.lat.nblocks, 1)));
   XCT_TRY(ar.get(&B.work, 1));
   XCT_TRY(ar.get(&B.rpart, (size_t)S_pad * kVecBlocks));
   XCT_TRY(ar.get(&B.log, (size_t)(iters + 1) * S_pad * 2));

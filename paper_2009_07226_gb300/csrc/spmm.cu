@@ -475,8 +475,6 @@ xct_status spmm(const SpmmArgs& a, cudaStream_t s) {
   return spmm_run(a, s);
 }
 
-int spmm_dot_count(const SpmmArgs& a) {
-  return spmm_pipe_applies(a) ? a.L->nblocks * kPipeConsumerWarps : a.L->nblocks;
-}
+int spmm_dot_count(const SpmmArgs& a) { return a.L->nblocks; }
 
 }  // namespace xct

@@ -63,7 +63,7 @@ struct PipeArgs {
   float* y;                  // [tile][nrows][ST]
   const uint32_t* in_max;
   int mat_scale_exp;
-  double* dot;               // [ntiles*ST][nblocks * NC] or null
+  double* dot;               // [ntiles*ST][nblocks] or null
   int* work;
   int* err;
   uint32_t xbytes, ebytes;   // per-buffer region sizes (128-byte multiples)
@@ -368,9 +368,10 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
         }
       }
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[buf]);
-    if (h.last) {
+    if (!h.last) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[buf]);
+    } else {
       // ---- epilogue of a block: de-normalise, write, squared norms ----
       const int tile = h.work / a.nblocks, b = h.work % a.nblocks;
       const int64_t row = (int64_t)b * kRowsPerBlock + rb;
@@ -399,6 +400,9 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
         }
       }
       if (a.dot) {
+        // per-slice squared norm of the block's rows: lanes sharing `sub`
+        // hold the same slices (reduce over rows by shuffles), then the 16
+        // consumer warps combine through shared memory in a fixed order
         double d[C::SPL];
 #pragma unroll
         for (int i = 0; i < C::SPL; ++i) d[i] = (double)r[i] * (double)r[i];
@@ -406,17 +410,32 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
         for (int o = C::LPR; o < 32; o <<= 1)
 #pragma unroll
           for (int i = 0; i < C::SPL; ++i) d[i] += __shfl_xor_sync(0xffffffffu, d[i], o);
+        // the staged rows of this buffer are no longer read once every
+        // consumer warp is here: their area holds the [NC][ST] partials
+        // (the buffer is released only after the reduction)
+        double* red = reinterpret_cast<double*>(xbuf(buf));
+        asm volatile("bar.sync 1, %0;" ::"r"(C::NC * 32) : "memory");   // consumers only
         if (rw == 0) {
-          const size_t nb = (size_t)a.nblocks * C::NC;
 #pragma unroll
           for (int v = 0; v < C::VPL; ++v)
 #pragma unroll
-            for (int e = 0; e < C::EPV; ++e) {
-              const int sl = v * C::LPR * C::EPV + sub * C::EPV + e;
-              a.dot[(size_t)(tile * ST + sl) * nb + (size_t)b * C::NC + warp] = d[v * C::EPV + e];
-            }
+            for (int e = 0; e < C::EPV; ++e)
+              red[warp * ST + v * C::LPR * C::EPV + sub * C::EPV + e] = d[v * C::EPV + e];
         }
+        asm volatile("bar.sync 1, %0;" ::"r"(C::NC * 32) : "memory");
+        if (warp == 0) {
+          for (int sl = lane; sl < ST; sl += 32) {
+            double t = 0.0;
+            for (int w = 0; w < C::NC; ++w) t += red[w * ST + sl];
+            a.dot[(size_t)(tile * ST + sl) * a.nblocks + b] = t;
+          }
+        }
+        // order these shared-memory writes before the copies that will refill
+        // the buffer once it is released
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[buf]);
     }
   }
 }
@@ -424,7 +443,6 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
 template <class TX, int ST>
 xct_status launch_pipe(const SpmmArgs& s, const unsigned char* src, cudaStream_t st) {
   using C = PCfg<TX, ST>;
-  static_assert(C::NC == kPipeConsumerWarps, "dot partial layout assumes 16 consumer warps");
   const Layout& L = *s.L;
   PipeArgs a;
   a.blk_stage = L.blk_stage;
@@ -449,6 +467,9 @@ xct_status launch_pipe(const SpmmArgs& s, const unsigned char* src, cudaStream_t
   a.ebytes = (uint32_t)(((size_t)L.emax_slots * C::EB + 127) / 128 * 128);
   const size_t listbytes = ((size_t)L.cap * 4 + 127) / 128 * 128;
   const size_t smem = 2 * ((size_t)a.xbytes + a.ebytes + 256 + 128) + 2 * listbytes + 64;
+  // the block-end reduction reuses a buffer's staged-row area
+  static_assert((size_t)C::NC * ST * sizeof(double) <= (size_t)65 * C::PIXB,
+                "reduction area must fit in the staged rows of the smallest stage buffer");
   static int configured_for = -1;
   if (configured_for != (int)smem) {
     XCT_TRY_CUDA(cudaFuncSetAttribute(spmm_pipe_kernel<TX, ST>,

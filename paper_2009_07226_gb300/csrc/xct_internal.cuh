@@ -114,7 +114,8 @@ inline size_t pipe_buffer_bytes(const Layout& L, int pixb) {
   return x + e + list + 128 * 2 + 256;
 }
 constexpr int kPipeCtasPerSm = 2;
-// shared memory one pipeline CTA may use (two buffers), kPipeCtasPerSm per SM
+// shared memory one pipeline CTA may use for its two buffers (the rest of its
+// 113 KB share goes to the barriers)
 constexpr size_t kPipeSmemLimit = 110 * 1024;
 
 struct Plan {
@@ -175,8 +176,8 @@ xct_status spmm_run(const SpmmArgs& a, cudaStream_t s);
 // apply to this layout / tile width (the caller then uses the staged form)
 bool spmm_pipe_applies(const SpmmArgs& a);
 xct_status spmm_pipe(const SpmmArgs& a, cudaStream_t s);
-constexpr int kPipeConsumerWarps = 16;
-// number of per-slice partial sums spmm() writes for dot_partial (per slice)
+// number of per-slice partial sums spmm() writes for dot_partial (per slice):
+// one per block of rows
 int spmm_dot_count(const SpmmArgs& a);
 bool spmm_supported(xct_dtype storage, int st);
 int pick_slices_per_tile(xct_dtype storage, int S);

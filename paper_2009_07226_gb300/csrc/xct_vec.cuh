@@ -6,7 +6,7 @@
 namespace xct {
 
 constexpr int kVecThreads = 256;
-constexpr int kVecBlocks = 256;   // blocks per slice tile of the vector kernels
+constexpr int kVecBlocks = 1024;  // blocks per slice tile of the vector kernels
 
 // Per-slice CGLS state on the device (FP64 scalars), [S_pad] each.
 struct CglsScalars {
