@@ -133,6 +133,75 @@ xct_status xct_backproject(xct_plan_t plan, const float* y, float* x,
 xct_status xct_cgls(xct_plan_t plan, const float* y, float* x, int32_t S,
                     int32_t iters, uint32_t flags, double* resid, void* stream);
 
+/*
+ * xct_tv -- smoothed total variation, the regulariser R(x) of Eq. 1 as this
+ * library reads it: TV_eps(x_s) = sum_{i,j} sqrt(dx^2 + dy^2 + eps^2) per
+ * slice with forward differences dx = x[i][j+1] - x[i][j], dy = x[i+1][j] -
+ * x[i][j] (0 past the last column / row).  One fused pass computes the value
+ * and the gradient.  x: device [S][n][n] float32.  grad: device [S][n][n]
+ * (overwritten with weight * dTV/dx) or NULL.  value: NULL or host/device
+ * double [S] receiving weight * TV_eps(x_s) (a host pointer makes the call
+ * synchronous).  eps > 0.
+ */
+xct_status xct_tv(const float* x, int32_t n, int32_t S, double eps, double weight,
+                  float* grad, double* value, void* stream);
+
+/*
+ * xct_adam -- one Adam step on `count` float32 parameters in place (the
+ * update of the gradient iteration of Sec. II-A for the regularised cost of
+ * Eq. 1): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * x -= lr / (1 - b1^step) * m / (sqrt(v) / sqrt(1 - b2^step) + eps).
+ * x, g, m, v: device pointers; step >= 1 counts from 1.
+ */
+xct_status xct_adam(float* x, const float* g, float* m, float* v, int64_t count, double lr,
+                    double beta1, double beta2, double eps, int32_t step, void* stream);
+
+/*
+ * xct_tv_reconstruct -- the regularised reconstruction of Eq. 1 with
+ * R(x) = lam * TV_eps(x): `steps` Adam steps (lr, beta1 0.9, beta2 0.999,
+ * eps 1e-8) on 0.5 ||y_s - A x_s||^2 + lam TV_eps(x_s), summed over slices.
+ * Each step projects, forms the residual, back projects it (the data-fit
+ * gradient), adds lam * grad TV_eps and updates x, all on the GPU.
+ * y: [S][M][N_d], x: [S][n][n] (in: start if flags & 1, else zeros; out:
+ * result), host or device.  loss: NULL or host/device double [steps] with the
+ * cost at each step before its update.  Synchronous.
+ */
+xct_status xct_tv_reconstruct(xct_plan_t plan, const float* y, float* x, int32_t S,
+                              int32_t steps, double lr, double lam, double eps, uint32_t flags,
+                              double* loss, void* stream);
+
+/* One job of a batched solve. */
+typedef struct {
+  xct_plan_t plan;   /* the job's geometry */
+  const float* y;    /* device [S][M][N_d] */
+  float* x;          /* device [S][n][n]: out (in as well with XCT_CGLS_X0) */
+  int32_t S;         /* slices of the job (0: skipped) */
+  int32_t reserved;
+  double* resid;     /* NULL or device [iters+1][S][2] (as xct_cgls) */
+} xct_job;
+
+#define XCT_BATCH_AUTOTUNE 8u  /* time the slice-tile widths per (plan, slices)
+                                  and keep the fastest (cached in the plan) */
+
+/*
+ * xct_cgls_batch -- `iters` CGLS iterations for every job (each slice its own
+ * least-squares problem, Eq. 1 with R = 0), jobs of uneven geometry and slice
+ * count solved together: jobs sharing a plan (geometry) are concatenated into
+ * one batch of slices (Sec. II-B: slices share A; Sec. III-A2: batches fused
+ * into minibatches); every product phase of all geometries with the same
+ * kernel configuration is one persistent launch over their combined work; the
+ * whole batch runs as one CUDA graph (unless XCT_CGLS_NO_GRAPH).  Flags:
+ * XCT_CGLS_X0, XCT_CGLS_NO_GRAPH, XCT_BATCH_AUTOTUNE.  Each job's result is
+ * bit-identical to xct_cgls on the concatenation of the slices of all jobs of
+ * its plan (same slice-tile width).  A slice whose A^T r_0 is zero stays at
+ * its start (no XCT_ERR_BREAKDOWN per job).  Plans must be distinct handles
+ * per geometry; a plan appearing in several jobs is one group.  Errors:
+ * XCT_ERR_INVALID (bad job, host buffer), XCT_ERR_OOM, XCT_ERR_CUDA,
+ * XCT_ERR_TIMEOUT (a bounded wait ran out; results invalid).  Synchronous.
+ */
+xct_status xct_cgls_batch(const xct_job* jobs, int32_t n_jobs, int32_t iters, uint32_t flags,
+                          void* stream);
+
 typedef struct {
   int64_t n_rays, n_pix, nnz;        /* rows of A, columns of A, entries */
   int32_t storage;                   /* xct_dtype */

@@ -446,3 +446,30 @@ def tv_value_grad(x: np.ndarray, eps: float):
     g[:, :, 1:] += ux[:, :, :-1]
     g[:, 1:, :] += uy[:, :-1, :]
     return val, g
+
+
+def adam_tv_reconstruct(a: CSR, at: CSR, y: np.ndarray, n: int, steps: int, lr: float, lam: float,
+                        eps: float, beta1: float = 0.9, beta2: float = 0.999, adam_eps: float = 1e-8,
+                        x0: np.ndarray | None = None):
+    """Regularised reconstruction of Eq. 1 with R(x) = lam * TV_eps(x), by the
+    gradient iteration of Sec. II-A (project, residual, back project, update)
+    with Adam (Kingma & Ba, bias-corrected, no weight decay) as the update.
+    Cost summed over slices: sum_s 0.5 ||A x_s - y_s||^2 + lam TV_eps(x_s).
+    y is [S, M*N_d]; returns (x [S, n*n], cost before each step [steps]), FP64."""
+    y = np.asarray(y, dtype=np.float64)
+    S = y.shape[0]
+    x = np.zeros((S, n * n)) if x0 is None else np.array(x0, dtype=np.float64).reshape(S, n * n)
+    m = np.zeros_like(x)
+    v = np.zeros_like(x)
+    hist = np.empty(steps)
+    for t in range(1, steps + 1):
+        r = project(a, x) - y
+        tv, tg = tv_value_grad(x.reshape(S, n, n), eps)
+        hist[t - 1] = 0.5 * float((r * r).sum()) + lam * tv
+        g = backproject(at, r) + lam * tg.reshape(S, -1)
+        m = beta1 * m + (1.0 - beta1) * g
+        v = beta2 * v + (1.0 - beta2) * g * g
+        mhat = m / (1.0 - beta1 ** t)
+        vhat = v / (1.0 - beta2 ** t)
+        x = x - lr * mhat / (np.sqrt(vhat) + adam_eps)
+    return x, hist

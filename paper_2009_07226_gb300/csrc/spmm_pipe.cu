@@ -44,13 +44,16 @@ struct PCfg {
 };
 
 struct __align__(16) Hdr {
-  int32_t work;    // work item (tile * nblocks + block), -1 = no more work
+  int32_t work;    // work item inside its product (tile * nblocks + block), -1 = no more work
   int32_t kstage;  // stage index inside the block
   int32_t last;    // last stage of the block
   int32_t np;      // staged rows (0: a block without entries)
+  int32_t prod;    // product index in the launch
+  int32_t pad[3];
 };
 
-struct PipeArgs {
+// One product of a launch: a layout with its input / output vectors.
+struct PipeLayout {
   const int64_t* blk_stage;
   const int64_t* stage_pix;
   const int64_t* stage_ent;
@@ -59,11 +62,19 @@ struct PipeArgs {
   const unsigned char* ent;
   int64_t nrows, ncols;
   int cap, nblocks, ntiles;
+  int work_begin;            // first work item of this product in the launch
   const unsigned char* xs;   // staged rows [tile][ncols][PIXB bytes]
   float* y;                  // [tile][nrows][ST]
   const uint32_t* in_max;
   int mat_scale_exp;
   double* dot;               // [ntiles*ST][nblocks] or null
+};
+
+struct PipeArgs {
+  PipeLayout L[kMaxPipeProducts];
+  int nl;                    // products in this launch
+  int nwork;                 // work items over all products
+  int cap;                   // largest stage capacity (buffer rows)
   int* work;
   int* err;
   uint32_t xbytes, ebytes;   // per-buffer region sizes (128-byte multiples)
@@ -190,38 +201,46 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
     mbar_init(&plbar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // zero slot (index cap) of both buffers: padding entries read 0.0 there
-  for (int i = tid; i < C::PIXB; i += C::NT) {
-    xbuf(0)[(size_t)a.cap * C::PIXB + i] = 0;
-    xbuf(1)[(size_t)a.cap * C::PIXB + i] = 0;
-  }
+  // zero slot of each product (row `cap` of its layout) in both buffers:
+  // padding entries read it with value 0
+  for (int l = 0; l < a.nl; ++l)
+    for (int i = tid; i < C::PIXB; i += C::NT) {
+      xbuf(0)[(size_t)a.L[l].cap * C::PIXB + i] = 0;
+      xbuf(1)[(size_t)a.L[l].cap * C::PIXB + i] = 0;
+    }
   __syncthreads();
 
-  const int nwork = a.nblocks * a.ntiles;
+  const int nwork = a.nwork;
 
   if (warp == C::NC) {
     // ----------------------------- producer -----------------------------
-    // A stage reference: work item, stage index in its block, stages in the
-    // block, layout stage (-1 for a block without entries); w = -1: no more.
-    struct Ref { int w, k, nst; int64_t s; };
+    // A stage reference: work item of the launch (-1: no more), its product
+    // and its work item inside the product, stage index in its block, stages
+    // in the block, layout stage (-1 for a block without entries).
+    struct Ref { int w, l, wl, k, nst; int64_t s; };
     auto fetch = [&]() -> Ref {
       int w = 0;
       if (lane == 0) w = atomicAdd(a.work, 1);
       w = __shfl_sync(0xffffffffu, w, 0);
-      if (w >= nwork) return Ref{-1, 0, 1, -1};
-      const int b = w % a.nblocks;
-      const int64_t s0 = a.blk_stage[b], s1 = a.blk_stage[b + 1];
-      return Ref{w, 0, s1 > s0 ? (int)(s1 - s0) : 1, s1 > s0 ? s0 : (int64_t)-1};
+      if (w >= nwork) return Ref{-1, 0, 0, 0, 1, -1};
+      int l = a.nl - 1;
+      while (l > 0 && w < a.L[l].work_begin) --l;
+      const PipeLayout& P = a.L[l];
+      const int wl = w - P.work_begin;
+      const int b = wl % P.nblocks;
+      const int64_t s0 = P.blk_stage[b], s1 = P.blk_stage[b + 1];
+      return Ref{w, l, wl, 0, s1 > s0 ? (int)(s1 - s0) : 1, s1 > s0 ? s0 : (int64_t)-1};
     };
     // the row-id list of stage r into list slot `slot` (one bulk copy; the
     // lists are 16-byte aligned and padded to 4 ids)
     auto request = [&](const Ref& r, int slot) {
       if (lane != 0) return;
       if (r.w >= 0 && r.s >= 0) {
-        const int64_t p0 = a.stage_pix[r.s];
-        const uint32_t n4 = (uint32_t)(((a.stage_pix[r.s + 1] - p0) + 3) & ~(int64_t)3);
+        const PipeLayout& P = a.L[r.l];
+        const int64_t p0 = P.stage_pix[r.s];
+        const uint32_t n4 = (uint32_t)(((P.stage_pix[r.s + 1] - p0) + 3) & ~(int64_t)3);
         mbar_arrive_tx(&plbar[slot], n4 * 4u);
-        bulk_g2s(plist(slot), a.pix + p0, n4 * 4u, &plbar[slot]);
+        bulk_g2s(plist(slot), P.pix + p0, n4 * 4u, &plbar[slot]);
       } else {
         mbar_arrive(&plbar[slot]);
       }
@@ -233,9 +252,11 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
     for (uint32_t it = 0;; ++it) {
       const int buf = it & 1;
       const uint32_t use = it >> 1;
-      Ref nxt{-1, 0, 1, -1};
+      Ref nxt{-1, 0, 0, 0, 1, -1};
       if (cur.w >= 0) {
-        nxt = (cur.k + 1 < cur.nst) ? Ref{cur.w, cur.k + 1, cur.nst, cur.s >= 0 ? cur.s + 1 : -1} : fetch();
+        nxt = (cur.k + 1 < cur.nst)
+                  ? Ref{cur.w, cur.l, cur.wl, cur.k + 1, cur.nst, cur.s >= 0 ? cur.s + 1 : -1}
+                  : fetch();
         // this warp's reads of list slot buf^1 (stage it-1) precede the copy into it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         request(nxt, buf ^ 1);
@@ -244,14 +265,16 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       const bool real = cur.w >= 0 && cur.s >= 0;
       if (real && !mbar_wait(&plbar[buf], use & 1)) { ok = false; break; }
-      const int tile = cur.w >= 0 ? cur.w / a.nblocks : 0;
-      const unsigned char* xt = a.xs + (size_t)tile * a.ncols * C::PIXB;
-      const int64_t p0 = real ? a.stage_pix[cur.s] : 0;
-      const int np = real ? (int)(a.stage_pix[cur.s + 1] - p0) : 0;
-      const uint32_t eb = real ? (uint32_t)((a.stage_ent[cur.s + 1] - a.stage_ent[cur.s]) * C::EB) : 0u;
+      const PipeLayout& P = a.L[cur.l];
+      const int tile = cur.w >= 0 ? cur.wl / P.nblocks : 0;
+      const unsigned char* xt = P.xs + (size_t)tile * P.ncols * C::PIXB;
+      const int64_t p0 = real ? P.stage_pix[cur.s] : 0;
+      const int np = real ? (int)(P.stage_pix[cur.s + 1] - p0) : 0;
+      const uint32_t eb = real ? (uint32_t)((P.stage_ent[cur.s + 1] - P.stage_ent[cur.s]) * C::EB) : 0u;
       if (lane == 0) {
         Hdr h;
-        h.work = cur.w;
+        h.work = cur.w >= 0 ? cur.wl : -1;
+        h.prod = cur.l;
         h.kstage = cur.k;
         h.last = (cur.k == cur.nst - 1);
         h.np = np;
@@ -279,11 +302,11 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
           }
         }
         // the stage's packed entries and its segment headers
-        const unsigned char* es = a.ent + (size_t)a.stage_ent[cur.s] * C::EB;
+        const unsigned char* es = P.ent + (size_t)P.stage_ent[cur.s] * C::EB;
         unsigned char* ed = ebuf(buf);
         for (uint32_t o = (uint32_t)lane * 16u; o < eb; o += 32u * 16u) cp16(ed + o, es + o);
         if (lane < 16)
-          cp16(sbuf(buf) + lane * 16, reinterpret_cast<const unsigned char*>(a.seg + cur.s * kQuads) + lane * 16);
+          cp16(sbuf(buf) + lane * 16, reinterpret_cast<const unsigned char*>(P.seg + cur.s * kQuads) + lane * 16);
       }
       cp_arrive_noinc(&full[buf]);
       if (lane == 0) mbar_arrive(&full[buf]);   // publishes the header
@@ -373,9 +396,10 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
       if (lane == 0) mbar_arrive(&empty[buf]);
     } else {
       // ---- epilogue of a block: de-normalise, write, squared norms ----
-      const int tile = h.work / a.nblocks, b = h.work % a.nblocks;
+      const PipeLayout& P = a.L[h.prod];
+      const int tile = h.work / P.nblocks, b = h.work % P.nblocks;
       const int64_t row = (int64_t)b * kRowsPerBlock + rb;
-      float* yt = a.y + (size_t)tile * a.nrows * ST;
+      float* yt = P.y + (size_t)tile * P.nrows * ST;
       float r[C::SPL];
 #pragma unroll
       for (int v = 0; v < C::VPL; ++v)
@@ -384,11 +408,11 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
           const int sl = v * C::LPR * C::EPV + sub * C::EPV + e;
           float scale = 1.0f;
           if (C::E16)
-            scale = ldexpf(1.0f, ceil_log2_exp_p(__uint_as_float(__ldg(a.in_max + tile * ST + sl))) -
-                                     a.mat_scale_exp);
+            scale = ldexpf(1.0f, ceil_log2_exp_p(__uint_as_float(__ldg(P.in_max + tile * ST + sl))) -
+                                     P.mat_scale_exp);
           r[v * C::EPV + e] = acc[v * C::EPV + e] * scale;
         }
-      if (row < a.nrows) {
+      if (row < P.nrows) {
 #pragma unroll
         for (int v = 0; v < C::VPL; ++v) {
           float* dst = yt + (size_t)row * ST + v * C::LPR * C::EPV + sub * C::EPV;
@@ -399,7 +423,7 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
                             r[v * C::EPV + 4 * q + 2], r[v * C::EPV + 4 * q + 3]);
         }
       }
-      if (a.dot) {
+      if (P.dot) {
         // per-slice squared norm of the block's rows: lanes sharing `sub`
         // hold the same slices (reduce over rows by shuffles), then the 16
         // consumer warps combine through shared memory in a fixed order
@@ -427,7 +451,7 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
           for (int sl = lane; sl < ST; sl += 32) {
             double t = 0.0;
             for (int w = 0; w < C::NC; ++w) t += red[w * ST + sl];
-            a.dot[(size_t)(tile * ST + sl) * a.nblocks + b] = t;
+            P.dot[(size_t)(tile * ST + sl) * P.nblocks + b] = t;
           }
         }
         // order these shared-memory writes before the copies that will refill
@@ -440,36 +464,67 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
   }
 }
 
+size_t pipe_smem_bytes(int cap, int64_t emax, int pixb, int eb, uint32_t* xbytes, uint32_t* ebytes) {
+  const size_t x = ((size_t)(cap + 1) * pixb + 127) / 128 * 128;
+  const size_t e = ((size_t)emax * eb + 127) / 128 * 128;
+  const size_t list = ((size_t)cap * 4 + 127) / 128 * 128;
+  if (xbytes) *xbytes = (uint32_t)x;
+  if (ebytes) *ebytes = (uint32_t)e;
+  return 2 * (x + e + 256 + 128) + 2 * list + 64;
+}
+
+// shared memory a pipeline CTA may use so that kPipeCtasPerSm fit on an SM
+constexpr size_t kPipeCtaSmemMax = 113 * 1024;
+
 template <class TX, int ST>
-xct_status launch_pipe(const SpmmArgs& s, const unsigned char* src, cudaStream_t st) {
+xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   using C = PCfg<TX, ST>;
-  const Layout& L = *s.L;
-  PipeArgs a;
-  a.blk_stage = L.blk_stage;
-  a.stage_pix = L.stage_pix;
-  a.stage_ent = L.stage_ent;
-  a.pix = L.pix;
-  a.seg = L.seg;
-  a.ent = static_cast<const unsigned char*>(L.ent);
-  a.nrows = L.nrows;
-  a.ncols = L.ncols;
-  a.cap = L.cap;
-  a.nblocks = L.nblocks;
-  a.ntiles = s.ntiles;
-  a.xs = src;
-  a.y = s.y;
-  a.in_max = s.in_max;
-  a.mat_scale_exp = s.mat_scale_exp;
-  a.dot = s.dot_partial;
-  a.work = s.work;
-  a.err = s.err;
-  a.xbytes = (uint32_t)(((size_t)(L.cap + 1) * C::PIXB + 127) / 128 * 128);
-  a.ebytes = (uint32_t)(((size_t)L.emax_slots * C::EB + 127) / 128 * 128);
-  const size_t listbytes = ((size_t)L.cap * 4 + 127) / 128 * 128;
-  const size_t smem = 2 * ((size_t)a.xbytes + a.ebytes + 256 + 128) + 2 * listbytes + 64;
   // the block-end reduction reuses a buffer's staged-row area
   static_assert((size_t)C::NC * ST * sizeof(double) <= (size_t)65 * C::PIXB,
                 "reduction area must fit in the staged rows of the smallest stage buffer");
+  if (count < 1 || count > kMaxPipeProducts) {
+    set_error("persistent product: %d products in one launch (1..%d)", count, kMaxPipeProducts);
+    return XCT_ERR_UNSUPPORTED;
+  }
+  PipeArgs a{};
+  int work = 0, cap = 0;
+  int64_t emax = 0;
+  for (int i = 0; i < count; ++i) {
+    const SpmmArgs& s = list[i];
+    const Layout& L = *s.L;
+    PipeLayout& P = a.L[i];
+    P.blk_stage = L.blk_stage;
+    P.stage_pix = L.stage_pix;
+    P.stage_ent = L.stage_ent;
+    P.pix = L.pix;
+    P.seg = L.seg;
+    P.ent = static_cast<const unsigned char*>(L.ent);
+    P.nrows = L.nrows;
+    P.ncols = L.ncols;
+    P.cap = L.cap;
+    P.nblocks = L.nblocks;
+    P.ntiles = s.ntiles;
+    P.work_begin = work;
+    P.xs = C::E16 ? reinterpret_cast<const unsigned char*>(s.staged16)
+                  : reinterpret_cast<const unsigned char*>(s.x);
+    P.y = s.y;
+    P.in_max = s.in_max;
+    P.mat_scale_exp = s.mat_scale_exp;
+    P.dot = s.dot_partial;
+    work += L.nblocks * s.ntiles;
+    cap = cap > L.cap ? cap : L.cap;
+    emax = emax > L.emax_slots ? emax : L.emax_slots;
+  }
+  a.nl = count;
+  a.nwork = work;
+  a.cap = cap;
+  a.work = list[0].work;
+  a.err = list[0].err;
+  const size_t smem = pipe_smem_bytes(cap, emax, C::PIXB, C::EB, &a.xbytes, &a.ebytes);
+  if (smem > kPipeCtaSmemMax) {
+    set_error("persistent product: %zu bytes of shared memory needed", smem);
+    return XCT_ERR_UNSUPPORTED;
+  }
   static int configured_for = -1;
   if (configured_for != (int)smem) {
     XCT_TRY_CUDA(cudaFuncSetAttribute(spmm_pipe_kernel<TX, ST>,
@@ -479,9 +534,9 @@ xct_status launch_pipe(const SpmmArgs& s, const unsigned char* src, cudaStream_t
   int dev = 0, sms = 0;
   XCT_TRY_CUDA(cudaGetDevice(&dev));
   XCT_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int nwork = L.nblocks * s.ntiles;
-  const int grid = nwork < sms * kPipeCtasPerSm ? nwork : sms * kPipeCtasPerSm;
-  XCT_TRY_CUDA(cudaMemsetAsync(s.work, 0, sizeof(int), st));
+  if (work == 0) return XCT_OK;
+  const int grid = work < sms * kPipeCtasPerSm ? work : sms * kPipeCtasPerSm;
+  XCT_TRY_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int), st));
   spmm_pipe_kernel<TX, ST><<<grid, C::NT, smem, st>>>(a);
   count_launch();
   XCT_TRY_CUDA(cudaGetLastError());
@@ -489,14 +544,27 @@ xct_status launch_pipe(const SpmmArgs& s, const unsigned char* src, cudaStream_t
 }
 
 template <class TX>
-xct_status dispatch_pipe(const SpmmArgs& s, const unsigned char* src, cudaStream_t st) {
+xct_status dispatch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   // the persistent form is built for 128-byte staged rows only
   constexpr int kST = 128 / PBytes<TX>::v;
-  if (s.st != kST) {
-    set_error("persistent product: unsupported tile width %d", s.st);
-    return XCT_ERR_UNSUPPORTED;
-  }
-  return launch_pipe<TX, kST>(s, src, st);
+  for (int i = 0; i < count; ++i)
+    if (list[i].st != kST) {
+      set_error("persistent product: unsupported tile width %d", list[i].st);
+      return XCT_ERR_UNSUPPORTED;
+    }
+  return launch_pipe<TX, kST>(list, count, st);
+}
+
+xct_status pipe_any(const SpmmArgs* list, int count, cudaStream_t s) {
+  const xct_dtype t = list[0].storage;
+  for (int i = 1; i < count; ++i)
+    if (list[i].storage != t) {
+      set_error("persistent product: products of one launch must share the storage type");
+      return XCT_ERR_INVALID;
+    }
+  if (t == XCT_F32) return dispatch_pipe<float>(list, count, s);
+  if (t == XCT_F16) return dispatch_pipe<__half>(list, count, s);
+  return dispatch_pipe<__nv_bfloat16>(list, count, s);
 }
 
 }  // namespace
@@ -507,14 +575,27 @@ bool spmm_pipe_applies(const SpmmArgs& a) {
   const int pixb = a.st * (a.storage == XCT_F32 ? 4 : 2);
   if (pixb != 128 || !a.work || !a.err) return false;
   if (a.L->nblocks == 0) return false;
-  return 2 * pipe_buffer_bytes(*a.L, 128) <= kPipeSmemLimit;
+  return pipe_smem_bytes(a.L->cap, a.L->emax_slots, 128, a.storage == XCT_F32 ? 8 : 4, nullptr,
+                         nullptr) <= kPipeCtaSmemMax;
 }
 
-xct_status spmm_pipe(const SpmmArgs& a, cudaStream_t s) {
-  const unsigned char* src = reinterpret_cast<const unsigned char*>(a.x);
-  if (a.storage == XCT_F32) return dispatch_pipe<float>(a, src, s);
-  if (a.storage == XCT_F16) return dispatch_pipe<__half>(a, reinterpret_cast<const unsigned char*>(a.staged16), s);
-  return dispatch_pipe<__nv_bfloat16>(a, reinterpret_cast<const unsigned char*>(a.staged16), s);
+xct_status spmm_pipe(const SpmmArgs& a, cudaStream_t s) { return pipe_any(&a, 1, s); }
+
+bool spmm_pipe_multi_applies(const SpmmArgs* list, int count) {
+  if (count < 1 || count > kMaxPipeProducts) return false;
+  int cap = 0;
+  int64_t emax = 0;
+  for (int i = 0; i < count; ++i) {
+    if (!spmm_pipe_applies(list[i]) || list[i].storage != list[0].storage) return false;
+    cap = cap > list[i].L->cap ? cap : list[i].L->cap;
+    emax = emax > list[i].L->emax_slots ? emax : list[i].L->emax_slots;
+  }
+  return pipe_smem_bytes(cap, emax, 128, list[0].storage == XCT_F32 ? 8 : 4, nullptr, nullptr) <=
+         kPipeCtaSmemMax;
+}
+
+xct_status spmm_pipe_multi(const SpmmArgs* list, int count, cudaStream_t s) {
+  return pipe_any(list, count, s);
 }
 
 }  // namespace xct

@@ -189,6 +189,52 @@ __global__ void __launch_bounds__(kVecThreads) residual_kernel(
   block_slice_sums<W>(ss, mx, st, tile, rpart, max_r, gridDim.x);
 }
 
+// r = q - y (data-fit residual of the regularised reconstruction); max |r|,
+// ||r||^2 partials
+template <int W>
+__global__ void __launch_bounds__(kVecThreads) sub_kernel(const float* __restrict__ q,
+                                                          const float* __restrict__ y,
+                                                          float* __restrict__ r, int64_t len, int st,
+                                                          uint32_t* __restrict__ max_r,
+                                                          double* __restrict__ rpart) {
+  const int tile = blockIdx.y;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * W;
+  const int64_t start = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * W;
+  const float* qt = q + (size_t)tile * len;
+  const float* yt = y + (size_t)tile * len;
+  float* rt = r + (size_t)tile * len;
+  double ss[W];
+  uint32_t mx[W];
+#pragma unroll
+  for (int w = 0; w < W; ++w) { ss[w] = 0.0; mx[w] = 0u; }
+  for (int64_t i = start; i < len; i += stride) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const float v = qt[i + w] - yt[i + w];
+      rt[i + w] = v;
+      ss[w] += (double)v * (double)v;
+      mx[w] = max(mx[w], __float_as_uint(fabsf(v)));
+    }
+  }
+  block_slice_sums<W>(ss, mx, st, tile, rpart, max_r, gridDim.x);
+}
+
+// loss = sum over slices s < S of 0.5 ||r_s||^2 + tv[s]  (one block)
+__global__ void loss_kernel(const double* __restrict__ rpart, int nbr, const double* __restrict__ tv,
+                            int S, double* __restrict__ out) {
+  __shared__ double sh[kVecThreads];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < S * nbr; i += blockDim.x) a += 0.5 * rpart[i];
+  for (int i = threadIdx.x; i < S; i += blockDim.x) a += tv[i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
 // ---------------------------------------------------------------------------
 // scalars: one block per slice, fixed-order tree reduction of partials
 // ---------------------------------------------------------------------------
@@ -312,6 +358,19 @@ xct_status cgls_update_p(float* p, const float* sv, int64_t npix, int st, int nt
 xct_status cgls_residual(float* r, const float* q, int64_t nray, int st, int ntiles,
                          uint32_t* max_r, double* rpart, cudaStream_t s) {
   XCT_VEC_LAUNCH(residual_kernel, r, q, nray * st, st, max_r, rpart);
+  return XCT_OK;
+}
+
+xct_status vec_sub_sumsq(const float* q, const float* y, float* r, int64_t rows, int st,
+                         int ntiles, uint32_t* max_r, double* rpart, cudaStream_t s) {
+  XCT_VEC_LAUNCH(sub_kernel, q, y, r, rows * st, st, max_r, rpart);
+  return XCT_OK;
+}
+
+xct_status vec_loss(const double* rpart, const double* tv, int S, double* out, cudaStream_t s) {
+  loss_kernel<<<1, kVecThreads, 0, s>>>(rpart, kVecBlocks, tv, S, out);
+  count_launch();
+  XCT_TRY_CUDA(cudaGetLastError());
   return XCT_OK;
 }
 

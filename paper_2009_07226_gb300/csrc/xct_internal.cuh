@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
 #include <vector>
 
 #include "xct.h"
@@ -137,6 +138,7 @@ struct Plan {
   int64_t* t_rowptr = nullptr; int32_t* t_col = nullptr; double* t_val = nullptr;
   Arena mem;                     // everything above lives here
   xct_stats stats{};
+  std::map<int, int> tile_choice;  // measured slice-tile width per slice count
 };
 
 // plan building (plan.cu)
@@ -176,11 +178,23 @@ xct_status spmm_run(const SpmmArgs& a, cudaStream_t s);
 // apply to this layout / tile width (the caller then uses the staged form)
 bool spmm_pipe_applies(const SpmmArgs& a);
 xct_status spmm_pipe(const SpmmArgs& a, cudaStream_t s);
+// several products (same storage type, 128-byte rows) in one persistent
+// launch sharing one work counter (list[0].work) -- the batched solver
+constexpr int kMaxPipeProducts = 8;
+bool spmm_pipe_multi_applies(const SpmmArgs* list, int count);
+xct_status spmm_pipe_multi(const SpmmArgs* list, int count, cudaStream_t s);
 // number of per-slice partial sums spmm() writes for dot_partial (per slice):
 // one per block of rows
 int spmm_dot_count(const SpmmArgs& a);
 bool spmm_supported(xct_dtype storage, int st);
 int pick_slices_per_tile(xct_dtype storage, int S);
+
+// regularisation (tv.cu)
+xct_status tv_launch(const float* x, int n, int S, double eps, double weight, float* grad,
+                     bool accumulate, double* partial, double* value_dev, cudaStream_t s);
+int tv_partials(int n);
+xct_status adam_launch(float* x, const float* g, float* m, float* v, int64_t count, double lr,
+                       double beta1, double beta2, double eps, int step, cudaStream_t s);
 
 // vector kernels (vec.cu)
 xct_status to_internal(const float* nat, float* in, const int32_t* inv_order,

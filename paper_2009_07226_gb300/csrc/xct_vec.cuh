@@ -26,6 +26,11 @@ xct_status cgls_update_p(float* p, const float* sv, int64_t npix, int st, int nt
                          const CglsScalars& sc, cudaStream_t s);
 xct_status cgls_residual(float* r, const float* q, int64_t nray, int st, int ntiles,
                          uint32_t* max_r, double* rpart, cudaStream_t s);
+// r = q - y on the internal layout, with max |r| and ||r||^2 partials
+// ([S_pad][kVecBlocks]); and the loss sum_s 0.5 ||r_s||^2 + tv[s] (s < S)
+xct_status vec_sub_sumsq(const float* q, const float* y, float* r, int64_t rows, int st,
+                         int ntiles, uint32_t* max_r, double* rpart, cudaStream_t s);
+xct_status vec_loss(const double* rpart, const double* tv, int S, double* out, cudaStream_t s);
 xct_status cgls_init_scalars(const double* gpart, int nbg, const double* rpart,
                              const CglsScalars& sc, double* log, int S_pad, cudaStream_t s);
 xct_status cgls_alpha(const double* dpart, int nbd, const CglsScalars& sc, int S_pad,

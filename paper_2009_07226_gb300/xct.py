@@ -54,6 +54,13 @@ class xct_stats(ctypes.Structure):
                 ("n_project", ctypes.c_int64), ("n_backproject", ctypes.c_int64)]
 
 
+class xct_job(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("y", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("S", ctypes.c_int32), ("reserved", ctypes.c_int32), ("resid", ctypes.c_void_p)]
+
+
+XCT_BATCH_AUTOTUNE = 8
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -68,6 +75,17 @@ _SIGNATURES = [
                                        ctypes.c_int32, ctypes.c_void_p]),
     ("xct_cgls", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                 ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
+    ("xct_tv", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                              ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("xct_adam", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, ctypes.c_int32, ctypes.c_void_p]),
+    ("xct_tv_reconstruct", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_uint32,
+                                          ctypes.c_void_p, ctypes.c_void_p]),
+    ("xct_cgls_batch", ctypes.c_int, [ctypes.POINTER(xct_job), ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_uint32, ctypes.c_void_p]),
     ("xct_plan_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(xct_stats)]),
     ("xct_plan_export", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.c_void_p, ctypes.c_void_p,
@@ -177,6 +195,32 @@ def xct_backproject(plan: int, y, x, S: int, stream=None) -> None:
 
 def xct_cgls(plan: int, y, x, S: int, iters: int, flags: int = 0, resid=None, stream=None) -> None:
     _check(lib().xct_cgls(plan, _ptr(y), _ptr(x), S, iters, flags, _ptr(resid), _stream(stream)))
+
+
+def xct_tv(x, n: int, S: int, eps: float, weight: float, grad=None, value=None, stream=None) -> None:
+    _check(lib().xct_tv(_ptr(x), n, S, eps, weight, _ptr(grad), _ptr(value), _stream(stream)))
+
+
+def xct_adam(x, g, m, v, count: int, lr: float, beta1: float, beta2: float, eps: float, step: int,
+             stream=None) -> None:
+    _check(lib().xct_adam(_ptr(x), _ptr(g), _ptr(m), _ptr(v), count, lr, beta1, beta2, eps, step,
+                          _stream(stream)))
+
+
+def xct_tv_reconstruct(plan: int, y, x, S: int, steps: int, lr: float, lam: float, eps: float,
+                       flags: int = 0, loss=None, stream=None) -> None:
+    _check(lib().xct_tv_reconstruct(plan, _ptr(y), _ptr(x), S, steps, lr, lam, eps, flags,
+                                    _ptr(loss), _stream(stream)))
+
+
+def xct_cgls_batch(jobs, iters: int, flags: int = 0, stream=None) -> None:
+    """jobs: sequence of (plan handle, y, x, S[, resid]) with device buffers."""
+    arr = (xct_job * max(len(jobs), 1))()
+    for i, jb in enumerate(jobs):
+        plan, y, x, S = jb[:4]
+        resid = jb[4] if len(jb) > 4 else None
+        arr[i] = xct_job(plan, _ptr(y), _ptr(x), S, 0, _ptr(resid))
+    _check(lib().xct_cgls_batch(arr, len(jobs), iters, flags, _stream(stream)))
 
 
 def xct_plan_stats(plan: int) -> dict:
