@@ -12,8 +12,9 @@ buffers, and the CPU oracle as a baseline.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Under torchrun (N > 1) every rank solves its own 64 slices (weak scaling;
-no data exchange) and rank 0 prints the max-over-ranks time.
+Under torchrun (N > 1) every rank solves its own 64 consecutive slices of a
+volume of 64 * N slices (weak scaling; no data exchange) and rank 0 prints
+the max-over-ranks time.
 """
 from __future__ import annotations
 
@@ -209,9 +210,12 @@ def run_ours(args):
     dev = torch.device("cuda", torch.cuda.current_device())
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2009_07226_gb300 import inputs, xct
+    from paper_2009_07226_gb300 import inputs, shard, xct
 
-    w = inputs.make_workload(WORKLOAD, slice_offset=rank * 64, with_images=False)
+    per_rank = inputs.WORKLOADS[WORKLOAD]["slices"]
+    first, count = shard.weak_range(per_rank, rank)
+    w = inputs.make_workload(WORKLOAD, slices=count, slice_offset=first, with_images=False,
+                             volume_slices=per_rank * world)
     n, m, nd, S, K = w["n"], w["m"], w["nd"], w["slices"], w["iters"]
     y = torch.tensor(w["sino"], dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
@@ -247,12 +251,7 @@ def run_ours(args):
         ev1.record(stream)
         barrier()
         launches = xct.xct_launch_count() - launches0
-        ms = ev0.elapsed_time(ev1) / steps
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = shard.max_over_ranks(ev0.elapsed_time(ev1) / steps, dev)
         return ms, tp / max(npj, 1), tb / max(nbp, 1), to / steps, launches
 
     for kind in ("f16", "f32"):
@@ -274,7 +273,7 @@ def run_ours(args):
     for _ in range(max(1, args.steps // 2)):
         step("f16", 0)
     torch.cuda.synchronize()
-    graph_ms = (time.perf_counter() - g0) / max(1, args.steps // 2) * 1e3
+    graph_ms = shard.max_over_ranks((time.perf_counter() - g0) / max(1, args.steps // 2) * 1e3, dev)
 
     # end to end through host buffers (pinned), H2D + solve + D2H every step
     yh = torch.tensor(w["sino"], dtype=torch.float32).pin_memory()
@@ -285,7 +284,7 @@ def run_ours(args):
     for _ in range(e2e_steps):
         xct.xct_cgls(plans["f16"].handle, yh, xh, S, K, 0, None, stream)
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - e0) / e2e_steps * 1e3
+    e2e_ms = shard.max_over_ranks((time.perf_counter() - e0) / e2e_steps * 1e3, dev)
 
     rel = float(torch.linalg.norm(xs["f16"] - xs["f32"]) / torch.linalg.norm(xs["f32"]))
 

@@ -40,6 +40,10 @@ WORKLOADS = {
     # differentiable, TV-regularised
     "tv3d_1024": dict(n=1024, m=720, nd=1024, slices=16, iters=200, seed=4,
                       phantom="ellipsoids", count=20, rho=(0.0, 1.0), noise=None),
+    # small 3D volume (slice-sharding checks on the host)
+    "small3d_64": dict(n=64, m=96, nd=64, slices=4, iters=10, seed=5,
+                       phantom="ellipsoids", count=20, rho=(0.0, 1.0),
+                       noise=("poisson", 1e4)),
 }
 
 
@@ -175,14 +179,15 @@ def gaussian_noise(rng: np.random.Generator, sino: np.ndarray, frac: float) -> n
 # ---------------------------------------------------------------------------
 
 def make_workload(name: str, slices: int | None = None, slice_offset: int = 0,
-                  with_images: bool = True):
+                  with_images: bool = True, volume_slices: int | None = None):
     """Phantom volume [S, n, n] (or None) and measured sinograms [S, m, nd]
     (float64) for one of WORKLOADS, seeded by the workload's seed.  Slices
-    [slice_offset, slice_offset + slices) of the full volume are produced, so
-    ranks sharing a volume get disjoint slice ranges of the same phantom."""
+    [slice_offset, slice_offset + slices) of a volume of `volume_slices`
+    slices (default: the workload's slice count) are produced, so ranks
+    sharing a volume get disjoint slice ranges of the same phantom."""
     w = WORKLOADS[name]
     n, m, nd = w["n"], w["m"], w["nd"]
-    total = w["slices"]
+    total = w["slices"] if volume_slices is None else volume_slices
     S = total if slices is None else slices
     cs = angle_table(m)
     rng = np.random.default_rng(w["seed"])
