@@ -386,6 +386,138 @@ def run_products(args):
                       "backproject_gflops": 2.0 * nnz * S / tb / 1e6}))
 
 
+def _job_sinos(jobs):
+    """Sinograms of the uneven batch, generated on the host cores (spawned
+    workers, before any GPU work)."""
+    from concurrent.futures import ProcessPoolExecutor
+    from multiprocessing import get_context
+
+    from paper_2009_07226_gb300 import inputs
+    with ProcessPoolExecutor(max_workers=os.cpu_count(), mp_context=get_context("spawn")) as ex:
+        return list(ex.map(inputs.job_sinograms, jobs))
+
+
+def run_batch(args):
+    """The uneven batch: 64 seeded jobs, N in {256, 384, 512, 768}, M = 1.5 N,
+    S ~ U{1..32}, 20 CGLS iterations each.  Mixed precision (binary16) in one
+    batched, graph-captured, autotuned call per step, against per-job FP32
+    calls (and the two other combinations, to separate batching from
+    precision)."""
+    from paper_2009_07226_gb300 import inputs
+    jobs = inputs.batch_jobs()
+    sinos = _job_sinos(jobs)
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_07226_gb300 import xct
+    K = inputs.BATCH["iters"]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    sizes = sorted({j["n"] for j in jobs})
+    plans = {(n, k): xct.Plan(n, 3 * n // 2, n, k, cos_sin=inputs.angle_table(3 * n // 2))
+             for n in sizes for k in ("f16", "f32")}
+    nnz = {n: plans[(n, "f32")].stats()["nnz"] for n in sizes}
+    ys = [torch.tensor(s, dtype=torch.float32, device=dev) for s in sinos]
+    xs = {k: [torch.empty((j["slices"], j["n"], j["n"]), device=dev) for j in jobs] for k in ("f16", "f32")}
+    flops = sum((2 * K + 1) * 2.0 * nnz[j["n"]] * j["slices"] for j in jobs)
+
+    def batched(kind):
+        xct.xct_cgls_batch([(plans[(j["n"], kind)].handle, ys[i], xs[kind][i], j["slices"])
+                            for i, j in enumerate(jobs)], K, xct.XCT_BATCH_AUTOTUNE, stream)
+
+    def per_job(kind):
+        for i, j in enumerate(jobs):
+            xct.xct_cgls(plans[(j["n"], kind)].handle, ys[i], xs[kind][i], j["slices"], K, 0, None, stream)
+
+    def timed(fn, kind):
+        for _ in range(args.warmup):
+            fn(kind)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = xct.xct_launch_count()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn(kind)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps, (xct.xct_launch_count() - l0) // args.steps
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    res = {}
+    for name, fn, kind in (("batched_mixed", batched, "f16"), ("per_job_fp32", per_job, "f32"),
+                           ("per_job_mixed", per_job, "f16"), ("batched_fp32", batched, "f32")):
+        ms, launches = timed(fn, kind)
+        res[name] = {"ms_per_step": ms, "gflops": flops / (ms * 1e-3) / 1e9, "gpu_launches": launches}
+    clocks = sampler.stop()
+    batched("f16")
+    per_job("f32")
+    torch.cuda.synchronize()
+    rel = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(xs["f16"], xs["f32"]))
+    print(json.dumps({
+        "mode": "batch", "metric": "proj+backproj GFLOP/s of the uneven batch (2*nnz*S per product)",
+        "jobs": len(jobs), "slices": sum(j["slices"] for j in jobs), "iters": K,
+        "slices_per_size": {n: sum(j["slices"] for j in jobs if j["n"] == n) for n in sizes},
+        "nnz": nnz, "flops_per_step": flops, **res,
+        "speedup_batched_mixed_vs_per_job_fp32": res["per_job_fp32"]["ms_per_step"] /
+                                                  res["batched_mixed"]["ms_per_step"],
+        "max_rel_diff_mixed_vs_fp32": rel, "clocks": clocks}))
+
+
+def run_tv(args):
+    """The regularised reconstruction: 1024^2 grid, 720 angles, 1024 bins,
+    16 slices, BF16 storage, 200 Adam steps on 0.5 ||A x - y||^2 +
+    1e-3 TV_eps (eps 1e-3, lr 1e-2), through the fused native loop and
+    through the autograd Functions (PyTorch loop around the same kernels)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_07226_gb300 import autograd as ag
+    from paper_2009_07226_gb300 import inputs, xct
+    w = inputs.make_workload("tv3d_1024", with_images=False)
+    n, m, nd, S, steps = w["n"], w["m"], w["nd"], w["slices"], w["iters"]
+    lam, eps, lr = 1e-3, 1e-3, 1e-2
+    stream = torch.cuda.current_stream()
+    plan = xct.Plan(n, m, nd, "bf16", cos_sin=w["cos_sin"])
+    nnz = plan.stats()["nnz"]
+    y = torch.tensor(w["sino"], dtype=torch.float32, device="cuda")
+    x = torch.empty((S, n, n), device="cuda")
+    loss = torch.zeros(steps, dtype=torch.float64, device="cuda")
+
+    def native():
+        xct.xct_tv_reconstruct(plan.handle, y, x, S, steps, lr, lam, eps, 0, loss, stream)
+
+    def autograd_loop():
+        ag.tv_reconstruct(plan, y, steps=steps, lr=lr, lam=lam, eps=eps)
+
+    res = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    for name, fn, reps in (("native", native, args.steps), ("autograd", autograd_loop, 1)):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = xct.xct_launch_count()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"ms_per_run": ms, "ms_per_adam_step": ms / steps,
+                     "gflops": steps * 2 * 2.0 * nnz * S / (ms * 1e-3) / 1e9,
+                     "gpu_launches_per_run": (xct.xct_launch_count() - l0) // reps}
+    clocks = sampler.stop()
+    native()
+    lh = loss.cpu().numpy()
+    print(json.dumps({"mode": "tv", "metric": "Adam steps/s and product GFLOP/s (2 products of "
+                      "2*nnz*S flops per step)", "n": n, "angles": m, "bins": nd, "slices": S,
+                      "steps": steps, "storage": "bf16", "nnz": nnz, **res,
+                      "cost_first": float(lh[0]), "cost_last": float(lh[-1]), "clocks": clocks}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,11 +525,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="cgls", choices=["cgls", "products"])
+    ap.add_argument("--mode", default="cgls", choices=["cgls", "products", "batch", "tv"])
     ap.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16"])
     args = ap.parse_args()
     if args.mode == "products":
         run_products(args)
+    elif args.mode == "batch":
+        run_batch(args)
+    elif args.mode == "tv":
+        run_tv(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -407,7 +407,7 @@ xct_status transpose(const int64_t* rowptr, const int32_t* col, const double* va
     while (p2 < hmax) p2 <<= 1;
     size_t smem = (size_t)p2 * 16;
     if (smem > 200 * 1024) {
-      set_error("a column holds %d entries; the transpose sort handles at most 12800", hmax);
+      set_error("a column holds %d entries; the transpose sort handles at most 8192", hmax);
       return XCT_ERR_UNSUPPORTED;
     }
     if (smem > 48 * 1024)

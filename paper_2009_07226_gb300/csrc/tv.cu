@@ -89,14 +89,18 @@ __global__ void tv_reduce_kernel(const double* __restrict__ partial, int nparts,
 // common reference implementation:
 //   m = b1 m + (1 - b1) g;  v = b2 v + (1 - b2) g^2
 //   x -= (lr / (1 - b1^t)) * m / (sqrt(v) / sqrt(1 - b2^t) + eps)
+// The weights 1 - b1, 1 - b2 and the bias corrections are formed in FP64 on
+// the host and rounded once to FP32 (1.0f - 0.9f would carry the rounding
+// of 0.9f into the weight).
 __global__ void adam_kernel(float* __restrict__ x, const float* __restrict__ g,
-                            float* __restrict__ m, float* __restrict__ v, int64_t count, float lr,
-                            float b1, float b2, float eps, float step_size, float bc2_sqrt) {
+                            float* __restrict__ m, float* __restrict__ v, int64_t count,
+                            float b1, float om1, float b2, float om2, float eps, float step_size,
+                            float bc2_sqrt) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count;
        k += (int64_t)gridDim.x * blockDim.x) {
     const float gk = g[k];
-    const float mk = b1 * m[k] + (1.0f - b1) * gk;
-    const float vk = b2 * v[k] + (1.0f - b2) * gk * gk;
+    const float mk = b1 * m[k] + om1 * gk;
+    const float vk = b2 * v[k] + om2 * gk * gk;
     m[k] = mk;
     v[k] = vk;
     const float denom = sqrtf(vk) / bc2_sqrt + eps;
@@ -133,8 +137,9 @@ xct_status adam_launch(float* x, const float* g, float* m, float* v, int64_t cou
   const double bc1 = 1.0 - pow(beta1, (double)step);
   const double bc2 = 1.0 - pow(beta2, (double)step);
   int blocks = (int)std::min<int64_t>((count + 255) / 256, 152 * 16);
-  adam_kernel<<<blocks, 256, 0, s>>>(x, g, m, v, count, (float)lr, (float)beta1, (float)beta2,
-                                     (float)eps, (float)(lr / bc1), (float)sqrt(bc2));
+  adam_kernel<<<blocks, 256, 0, s>>>(x, g, m, v, count, (float)beta1, (float)(1.0 - beta1),
+                                     (float)beta2, (float)(1.0 - beta2), (float)eps,
+                                     (float)(lr / bc1), (float)sqrt(bc2));
   count_launch();
   XCT_TRY_CUDA(cudaGetLastError());
   return XCT_OK;

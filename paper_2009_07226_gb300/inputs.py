@@ -210,3 +210,37 @@ def make_workload(name: str, slices: int | None = None, slice_offset: int = 0,
             sino[s] = gaussian_noise(nrng, sino[s], noise[1])
     return dict(n=n, m=m, nd=nd, slices=S, iters=w["iters"], cos_sin=cs,
                 images=imgs, sino=sino)
+
+
+# ---------------------------------------------------------------------------
+# Uneven batch of reconstruction jobs
+# ---------------------------------------------------------------------------
+
+BATCH = dict(count=64, sizes=(256, 384, 512, 768), max_slices=32, iters=20, seed=6,
+             ellipses=10, photons=1e4)
+
+
+def batch_jobs(count: int = BATCH["count"], seed: int = BATCH["seed"],
+               sizes=BATCH["sizes"], max_slices: int = BATCH["max_slices"]) -> list:
+    """Seeded job list of the uneven batch: grid side N drawn uniformly from
+    `sizes`, M = 1.5 N angles on [0, pi), N unit bins, S ~ U{1..max_slices}."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for j in range(count):
+        n = int(sizes[int(rng.integers(len(sizes)))])
+        S = int(rng.integers(1, max_slices + 1))
+        jobs.append(dict(n=n, m=3 * n // 2, nd=n, slices=S, seed=1000 * seed + j))
+    return jobs
+
+
+def job_sinograms(job: dict, photons: float = BATCH["photons"],
+                  ellipses: int = BATCH["ellipses"]) -> np.ndarray:
+    """[S, m, nd] float64 measured sinograms of one batch job: slice s is its
+    own random ellipse phantom (seeded by (job seed, s)) with Poisson noise."""
+    cs = angle_table(job["m"])
+    out = np.empty((job["slices"], job["m"], job["nd"]))
+    for s in range(job["slices"]):
+        rng = np.random.default_rng([job["seed"], s])
+        ells = random_ellipses(rng, ellipses)
+        out[s] = poisson_noise(rng, line_integrals(ells, job["n"], cs, job["nd"]), job["n"], photons)
+    return out
