@@ -4,15 +4,15 @@
 //
 // Two CTAs per SM.  A producer warp takes blocks of 64 rows from a work
 // counter and streams each stage of each block into one of two shared-memory
-// buffers with bulk asynchronous copies (cp.async.bulk, completion counted in
-// bytes on an mbarrier): the block's staged input rows for the stage (one
-// 16..128-byte copy per row), the stage's packed entries and its segment
-// headers (one copy each).  Sixteen consumer warps compute from shared memory
-// only and release the buffer through a second mbarrier; while they work on
-// one stage the next one (possibly of the next block) is already in flight.
-// The lane layout of the consumers is the one of spmm.cu: a group of lanes
-// holds different slices of one row, so every shared-memory wavefront reads
-// one contiguous staged row.
+// buffers: the stage's staged input rows are gathered with 16-byte cp.async
+// copies (one or two lanes per 128-byte row, from a row-id list fetched one
+// stage ahead by a bulk copy), its packed entries and segment headers arrive
+// as two bulk copies (cp.async.bulk) counted in bytes on the same mbarrier.
+// Sixteen consumer warps compute from shared memory only and release the
+// buffer through a second mbarrier; while they work on one stage the next one
+// (possibly of the next block) is already in flight.  The lane layout of the
+// consumers is the one of spmm.cu: a group of lanes holds different slices of
+// one row, so every shared-memory wavefront reads one contiguous staged row.
 //
 // Every wait is bounded (about two seconds of wall time); a wait that runs out
 // sets the caller's error flag, waits (bounded) for the copies this CTA has in
@@ -41,6 +41,10 @@ struct PCfg {
   static constexpr int NT = (NC + 1) * 32;         // + one producer warp
   static constexpr bool E16 = XB == 2;
   static constexpr int EB = E16 ? 4 : 8;           // bytes per packed entry
+  // producer lanes per staged row: each lane copies PIXB / PL bytes of its
+  // row (fewer lanes per row: fewer producer instructions per stage; measured
+  // best at one lane per row for 16-bit rows, two for FP32 rows)
+  static constexpr int PL = E16 ? 1 : 2;
 };
 
 struct __align__(16) Hdr {
@@ -127,6 +131,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 __device__ __forceinline__ void cp16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
+}
+// 16-byte copy at a constant byte offset from both addresses
+template <int OFF>
+__device__ __forceinline__ void cp16_at(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0+%2], [%1+%2], 16;" ::"r"(dst), "l"(src), "n"(OFF)
+               : "memory");
 }
 // arrive on `bar` once every cp.async this thread issued so far has landed
 __device__ __forceinline__ void cp_arrive_noinc(uint64_t* bar) {
@@ -216,47 +226,69 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
     // ----------------------------- producer -----------------------------
     // A stage reference: work item of the launch (-1: no more), its product
     // and its work item inside the product, stage index in its block, stages
-    // in the block, layout stage (-1 for a block without entries).
-    struct Ref { int w, l, wl, k, nst; int64_t s; };
+    // in the block, layout stage (-1 for a block without entries), and the
+    // stage's staged rows and packed entries (loaded when the reference is
+    // made, one stage ahead of its copies).
+    struct Ref {
+      int w, l, wl, k, nst;
+      int64_t s;
+      int64_t p0, e0;
+      int np;
+      uint32_t eb;
+    };
+    auto meta = [&](Ref& r) {
+      r.p0 = 0; r.e0 = 0; r.np = 0; r.eb = 0;
+      if (r.w >= 0 && r.s >= 0) {
+        const PipeLayout& P = a.L[r.l];
+        r.p0 = P.stage_pix[r.s];
+        r.np = (int)(P.stage_pix[r.s + 1] - r.p0);
+        r.e0 = P.stage_ent[r.s];
+        r.eb = (uint32_t)((P.stage_ent[r.s + 1] - r.e0) * C::EB);
+      }
+    };
     auto fetch = [&]() -> Ref {
       int w = 0;
       if (lane == 0) w = atomicAdd(a.work, 1);
       w = __shfl_sync(0xffffffffu, w, 0);
-      if (w >= nwork) return Ref{-1, 0, 0, 0, 1, -1};
+      Ref r{-1, 0, 0, 0, 1, -1, 0, 0, 0, 0u};
+      if (w >= nwork) return r;
       int l = a.nl - 1;
       while (l > 0 && w < a.L[l].work_begin) --l;
       const PipeLayout& P = a.L[l];
       const int wl = w - P.work_begin;
       const int b = wl % P.nblocks;
       const int64_t s0 = P.blk_stage[b], s1 = P.blk_stage[b + 1];
-      return Ref{w, l, wl, 0, s1 > s0 ? (int)(s1 - s0) : 1, s1 > s0 ? s0 : (int64_t)-1};
+      r = Ref{w, l, wl, 0, s1 > s0 ? (int)(s1 - s0) : 1, s1 > s0 ? s0 : (int64_t)-1, 0, 0, 0, 0u};
+      meta(r);
+      return r;
     };
     // the row-id list of stage r into list slot `slot` (one bulk copy; the
     // lists are 16-byte aligned and padded to 4 ids)
     auto request = [&](const Ref& r, int slot) {
       if (lane != 0) return;
       if (r.w >= 0 && r.s >= 0) {
-        const PipeLayout& P = a.L[r.l];
-        const int64_t p0 = P.stage_pix[r.s];
-        const uint32_t n4 = (uint32_t)(((P.stage_pix[r.s + 1] - p0) + 3) & ~(int64_t)3);
+        const uint32_t n4 = (uint32_t)((r.np + 3) & ~3);
         mbar_arrive_tx(&plbar[slot], n4 * 4u);
-        bulk_g2s(plist(slot), P.pix + p0, n4 * 4u, &plbar[slot]);
+        bulk_g2s(plist(slot), a.L[r.l].pix + r.p0, n4 * 4u, &plbar[slot]);
       } else {
         mbar_arrive(&plbar[slot]);
       }
     };
     bool ok = true;
-    int issued[2] = {-1, -1};  // last use of each buffer with copies in flight
+    int issued0 = -1, issued1 = -1;  // last use of each buffer with copies in flight
     Ref cur = fetch();
     request(cur, 0);
     for (uint32_t it = 0;; ++it) {
       const int buf = it & 1;
       const uint32_t use = it >> 1;
-      Ref nxt{-1, 0, 0, 0, 1, -1};
+      Ref nxt{-1, 0, 0, 0, 1, -1, 0, 0, 0, 0u};
       if (cur.w >= 0) {
-        nxt = (cur.k + 1 < cur.nst)
-                  ? Ref{cur.w, cur.l, cur.wl, cur.k + 1, cur.nst, cur.s >= 0 ? cur.s + 1 : -1}
-                  : fetch();
+        if (cur.k + 1 < cur.nst) {
+          nxt = Ref{cur.w, cur.l, cur.wl, cur.k + 1, cur.nst, cur.s >= 0 ? cur.s + 1 : -1, 0, 0, 0, 0u};
+          meta(nxt);
+        } else {
+          nxt = fetch();
+        }
         // this warp's reads of list slot buf^1 (stage it-1) precede the copy into it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         request(nxt, buf ^ 1);
@@ -268,9 +300,8 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
       const PipeLayout& P = a.L[cur.l];
       const int tile = cur.w >= 0 ? cur.wl / P.nblocks : 0;
       const unsigned char* xt = P.xs + (size_t)tile * P.ncols * C::PIXB;
-      const int64_t p0 = real ? P.stage_pix[cur.s] : 0;
-      const int np = real ? (int)(P.stage_pix[cur.s + 1] - p0) : 0;
-      const uint32_t eb = real ? (uint32_t)((P.stage_ent[cur.s + 1] - P.stage_ent[cur.s]) * C::EB) : 0u;
+      const int np = real ? cur.np : 0;
+      const uint32_t eb = real ? cur.eb : 0u;
       if (lane == 0) {
         Hdr h;
         h.work = cur.w >= 0 ? cur.wl : -1;
@@ -281,43 +312,50 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
         *hbuf(buf) = h;
       }
       if (real) {
-        issued[buf] = (int)use;
-        // staged rows: 16-byte pieces, PPR lanes per row, RPI rows per instruction
-        constexpr int PPR = C::PIXB / 16;
-        constexpr int RPI = 32 / PPR;
-        unsigned char* xd = xbuf(buf);
+        if (buf) issued1 = (int)use; else issued0 = (int)use;
+        // staged rows: PL lanes per row; instruction j copies bytes
+        // [16 PL j, 16 PL (j+1)) of RPI rows
+        constexpr int PL = C::PL;
+        constexpr int RPI = 32 / PL;
+        const int pr = lane / PL, pc = lane % PL;
+        const uint32_t xd = su32(xbuf(buf)) + (uint32_t)(pr * C::PIXB + pc * 16);
         const int32_t* pl = plist(buf);
-        const int pr = lane / PPR, pc = lane % PPR;
-        for (int r0 = 0; r0 < np; r0 += RPI * 8) {
-          int32_t gp[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int r = r0 + j * RPI + pr;
-            gp[j] = r < np ? pl[r] : 0;
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int r = r0 + j * RPI + pr;
-            if (r < np) cp16(xd + (size_t)r * C::PIXB + pc * 16, xt + (size_t)gp[j] * C::PIXB + pc * 16);
+        const unsigned char* xs0 = xt + pc * 16;
+        for (int r = pr; r < np; r += RPI) {
+          const unsigned char* src = xs0 + (size_t)pl[r] * C::PIXB;
+          const uint32_t dst = xd + (uint32_t)((r - pr) * C::PIXB);
+          cp16_at<0>(dst, src);
+          if constexpr (C::PIXB > PL * 16) cp16_at<PL * 16>(dst, src);
+          if constexpr (C::PIXB > 2 * PL * 16) cp16_at<2 * PL * 16>(dst, src);
+          if constexpr (C::PIXB > 3 * PL * 16) cp16_at<3 * PL * 16>(dst, src);
+          if constexpr (C::PIXB > 4 * PL * 16) {
+            cp16_at<4 * PL * 16>(dst, src);
+            cp16_at<5 * PL * 16>(dst, src);
+            cp16_at<6 * PL * 16>(dst, src);
+            cp16_at<7 * PL * 16>(dst, src);
           }
         }
-        // the stage's packed entries and its segment headers
-        const unsigned char* es = P.ent + (size_t)P.stage_ent[cur.s] * C::EB;
-        unsigned char* ed = ebuf(buf);
-        for (uint32_t o = (uint32_t)lane * 16u; o < eb; o += 32u * 16u) cp16(ed + o, es + o);
-        if (lane < 16)
-          cp16(sbuf(buf) + lane * 16, reinterpret_cast<const unsigned char*>(P.seg + cur.s * kQuads) + lane * 16);
       }
       cp_arrive_noinc(&full[buf]);
-      if (lane == 0) mbar_arrive(&full[buf]);   // publishes the header
+      if (lane == 0) {
+        // the stage's packed entries and segment headers: two bulk copies
+        // counted in bytes; this arrival also publishes the header
+        if (real) {
+          mbar_arrive_tx(&full[buf], eb + 256u);
+          if (eb) bulk_g2s(ebuf(buf), P.ent + (size_t)cur.e0 * C::EB, eb, &full[buf]);
+          bulk_g2s(sbuf(buf), P.seg + cur.s * kQuads, 256u, &full[buf]);
+        } else {
+          mbar_arrive(&full[buf]);
+        }
+      }
       if (cur.w < 0) break;
       cur = nxt;
     }
     if (!ok) {
       if (lane == 0) atomicExch(a.err, 1);
       // let copies already issued land before the CTA's shared memory goes away
-      for (int buf = 0; buf < 2; ++buf)
-        if (issued[buf] >= 0) mbar_wait(&full[buf], (uint32_t)issued[buf] & 1);
+      if (issued0 >= 0) mbar_wait(&full[0], (uint32_t)issued0 & 1);
+      if (issued1 >= 0) mbar_wait(&full[1], (uint32_t)issued1 & 1);
     }
     return;
   }
