@@ -328,11 +328,18 @@ def hilbert_index(side: int, x: int, y: int) -> int:
     return d
 
 
-def hilbert_order(nx: int, ny: int, tile: int) -> np.ndarray:
+def hilbert_order(nx: int, ny: int, tile: int, inner: str = "row") -> np.ndarray:
     """Map natural id (y * nx + x) -> ordered id.  Cells are grouped in
     tile x tile squares (ragged at the far edges); squares are ordered by
     their Hilbert position on the smallest power-of-two square grid that
-    holds them; cells inside a square are numbered row-major."""
+    holds them; cells inside a square are numbered by `inner`:
+      'row'  -- row-major (x fastest);
+      'col'  -- column-major (y fastest);
+      'quad' -- 2 x 2 groups of cells, the groups row-major and the cells of
+                a group row-major (squares with an odd width or height are
+                numbered row-major)."""
+    if inner not in ("row", "col", "quad"):
+        raise ValueError(inner)
     ntx = -(-nx // tile)
     nty = -(-ny // tile)
     side = 1
@@ -349,7 +356,14 @@ def hilbert_order(nx: int, ny: int, tile: int) -> np.ndarray:
         x0, y0 = tx * tile, ty * tile
         w = min(tile, nx - x0)
         h = min(tile, ny - y0)
-        perm[y0:y0 + h, x0:x0 + w] = nxt + np.arange(h * w, dtype=np.int64).reshape(h, w)
+        ly, lx = np.mgrid[0:h, 0:w]
+        if inner == "col":
+            local = lx * h + ly
+        elif inner == "quad" and w % 2 == 0 and h % 2 == 0:
+            local = ((ly // 2) * (w // 2) + lx // 2) * 4 + (ly % 2) * 2 + lx % 2
+        else:
+            local = ly * w + lx
+        perm[y0:y0 + h, x0:x0 + w] = nxt + local
         nxt += h * w
     return perm.reshape(-1)
 

@@ -58,6 +58,11 @@ __device__ int64_t hilbert_pos(int64_t side, int64_t x, int64_t y) {
   return d;
 }
 
+// numbering inside a tile
+constexpr int kInnerRow = 0;    // x fastest
+constexpr int kInnerCol = 1;    // y fastest
+constexpr int kInnerQuad = 2;   // 2 x 2 groups, row-major (row-major if a side is odd)
+
 __global__ void tile_sizes_kernel(int64_t nx, int64_t ny, int64_t T, int64_t ntx, int64_t nty,
                                   int64_t side, int64_t* tile_size) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -67,19 +72,27 @@ __global__ void tile_sizes_kernel(int64_t nx, int64_t ny, int64_t T, int64_t ntx
   tile_size[hilbert_pos(side, tx, ty)] = w * h;
 }
 
-__global__ void order_kernel(int64_t nx, int64_t ny, int64_t T, int64_t side,
+__global__ void order_kernel(int64_t nx, int64_t ny, int64_t T, int64_t side, int inner,
                              const int64_t* tile_off, int32_t* order, int32_t* inv) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= nx * ny) return;
   int64_t x = i % nx, y = i / nx;
   int64_t tx = x / T, ty = y / T;
-  int64_t w = min(T, nx - tx * T);
-  int64_t id = tile_off[hilbert_pos(side, tx, ty)] + (y - ty * T) * w + (x - tx * T);
+  int64_t w = min(T, nx - tx * T), h = min(T, ny - ty * T);
+  int64_t lx = x - tx * T, ly = y - ty * T;
+  int64_t local;
+  if (inner == kInnerCol)
+    local = lx * h + ly;
+  else if (inner == kInnerQuad && w % 2 == 0 && h % 2 == 0)
+    local = ((ly / 2) * (w / 2) + lx / 2) * 4 + (ly % 2) * 2 + lx % 2;
+  else
+    local = ly * w + lx;
+  int64_t id = tile_off[hilbert_pos(side, tx, ty)] + local;
   order[i] = (int32_t)id;
   inv[id] = (int32_t)i;
 }
 
-xct_status make_order(int64_t nx, int64_t ny, int64_t T, int32_t* order, int32_t* inv,
+xct_status make_order(int64_t nx, int64_t ny, int64_t T, int inner, int32_t* order, int32_t* inv,
                       cudaStream_t s) {
   const int64_t ntx = (nx + T - 1) / T, nty = (ny + T - 1) / T;
   int64_t side = 1;
@@ -97,7 +110,7 @@ xct_status make_order(int64_t nx, int64_t ny, int64_t T, int32_t* order, int32_t
   tile_sizes_kernel<<<grid_for(ntx * nty, 256), 256, 0, s>>>(nx, ny, T, ntx, nty, side, tsz);
   count_launch();
   XCT_TRY(exclusive_scan_i64(tsz, toff, side * side, s));
-  order_kernel<<<grid_for(nx * ny, 256), 256, 0, s>>>(nx, ny, T, side, toff, order, inv);
+  order_kernel<<<grid_for(nx * ny, 256), 256, 0, s>>>(nx, ny, T, side, inner, toff, order, inv);
   count_launch();
   XCT_TRY_CUDA(cudaGetLastError());
   return XCT_OK;
@@ -831,8 +844,13 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
   XCT_TRY(keep.get(&p.pix_inv, p.npix));
   XCT_TRY(keep.get(&p.ray_order, p.nray));
   XCT_TRY(keep.get(&p.ray_inv, p.nray));
-  XCT_TRY(make_order(g.n, g.n, T, p.pix_order, p.pix_inv, s));
-  XCT_TRY(make_order(g.n_det, g.n_angles, T, p.ray_order, p.ray_inv, s));
+  // Inside a tile: pixels in 2 x 2 groups, rays angle-fastest.  Four
+  // consecutive rows of A (or A^T) form one quad of the packed layout, padded
+  // to its longest row per stage; neighbouring angles through one bin (and
+  // 2 x 2 pixel groups) cross a stage's pixels (rays) more evenly than four
+  // neighbouring bins (a 1 x 4 pixel run), so less padding.
+  XCT_TRY(make_order(g.n, g.n, T, kInnerQuad, p.pix_order, p.pix_inv, s));
+  XCT_TRY(make_order(g.n_det, g.n_angles, T, kInnerCol, p.ray_order, p.ray_inv, s));
 
   GeomDev gd{g.n, g.n_angles, g.n_det, g.det_spacing, g.det_offset, g.min_seg, cs_dev};
   int32_t* cnt;
@@ -862,19 +880,19 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
   XCT_TRY(f64.get(&tval, p.nnz));
   XCT_TRY(transpose(rowptr, col, val, p.nray, p.npix, p.nnz, colptr, trow, tval, s));
 
-  // Stage capacity: two pipeline buffers (128-byte staged rows plus the
+  // Stage capacity: the pipeline buffers (128-byte staged rows plus the
   // stage's packed entries) must fit in shared memory; a layout whose largest
   // stage does not fit is rebuilt with a smaller capacity.
   CsrView ma{rowptr, col, val, p.nray, p.npix};
   CsrView mt{colptr, trow, tval, p.npix, p.nray};
-  int32_t cap = p.storage == XCT_F32 ? 200 : 280;
+  int32_t cap = p.storage == XCT_F32 ? kPipeCap32 : kPipeCap16;
   for (int attempt = 0;; ++attempt) {
     Arena la_mem(s), lat_mem(s);
     Layout la, lat;
     XCT_TRY(build_layout(ma, p.nnz, p.storage, cap, la, la_mem, s));
     XCT_TRY(build_layout(mt, p.nnz, p.storage, cap, lat, lat_mem, s));
-    const bool fits = 2 * pipe_buffer_bytes(la, 128) <= kPipeSmemLimit &&
-                      2 * pipe_buffer_bytes(lat, 128) <= kPipeSmemLimit;
+    const bool fits = kPipeBufs * pipe_buffer_bytes(la, 128) <= kPipeSmemLimit &&
+                      kPipeBufs * pipe_buffer_bytes(lat, 128) <= kPipeSmemLimit;
     if (fits || attempt == 3 || cap <= 64) {
       p.la = la;
       p.lat = lat;

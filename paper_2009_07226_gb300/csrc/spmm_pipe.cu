@@ -191,10 +191,11 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t bufbytes = a.xbytes + a.ebytes + 256 + 128;
   const uint32_t listbytes = (uint32_t)(((size_t)a.cap * 4 + 127) / 128 * 128);
-  int32_t* lists = reinterpret_cast<int32_t*>(smem + 2 * bufbytes);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * bufbytes + 2 * listbytes);
-  uint64_t* empty = full + 2;
-  uint64_t* plbar = full + 4;   // row-id list of a stage landed
+  constexpr int NB = kPipeBufs;
+  int32_t* lists = reinterpret_cast<int32_t*>(smem + NB * bufbytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NB * bufbytes + NB * listbytes);
+  uint64_t* empty = full + NB;
+  uint64_t* plbar = full + 2 * NB;   // row-id list of a stage landed
   auto plist = [&](int slot) { return lists + (size_t)slot * (listbytes / 4); };
   auto xbuf = [&](int b) { return smem + b * bufbytes; };
   auto ebuf = [&](int b) { return smem + b * bufbytes + a.xbytes; };
@@ -203,21 +204,18 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    mbar_init(&full[0], 33);
-    mbar_init(&full[1], 33);
-    mbar_init(&empty[0], C::NC);
-    mbar_init(&empty[1], C::NC);
-    mbar_init(&plbar[0], 1);
-    mbar_init(&plbar[1], 1);
+    for (int b = 0; b < NB; ++b) {
+      mbar_init(&full[b], 33);
+      mbar_init(&empty[b], C::NC);
+      mbar_init(&plbar[b], 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // zero slot of each product (row `cap` of its layout) in both buffers:
+  // zero slot of each product (row `cap` of its layout) in every buffer:
   // padding entries read it with value 0
   for (int l = 0; l < a.nl; ++l)
-    for (int i = tid; i < C::PIXB; i += C::NT) {
-      xbuf(0)[(size_t)a.L[l].cap * C::PIXB + i] = 0;
-      xbuf(1)[(size_t)a.L[l].cap * C::PIXB + i] = 0;
-    }
+    for (int i = tid; i < C::PIXB; i += C::NT)
+      for (int b = 0; b < NB; ++b) xbuf(b)[(size_t)a.L[l].cap * C::PIXB + i] = 0;
   __syncthreads();
 
   const int nwork = a.nwork;
@@ -275,12 +273,12 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
       }
     };
     bool ok = true;
-    int issued0 = -1, issued1 = -1;  // last use of each buffer with copies in flight
+    uint32_t fail_it = 0;
     Ref cur = fetch();
     request(cur, 0);
     for (uint32_t it = 0;; ++it) {
-      const int buf = it & 1;
-      const uint32_t use = it >> 1;
+      const int buf = (int)(it % NB);
+      const uint32_t use = it / NB;
       Ref nxt{-1, 0, 0, 0, 1, -1, 0, 0, 0, 0u};
       if (cur.w >= 0) {
         if (cur.k + 1 < cur.nst) {
@@ -289,14 +287,15 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
         } else {
           nxt = fetch();
         }
-        // this warp's reads of list slot buf^1 (stage it-1) precede the copy into it
+        // this warp's reads of the next list slot (stage it+1-NB) precede
+        // the copy into it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        request(nxt, buf ^ 1);
+        request(nxt, buf + 1 == NB ? 0 : buf + 1);
       }
-      if (!mbar_wait(&empty[buf], (use & 1) ^ 1)) { ok = false; break; }
+      if (!mbar_wait(&empty[buf], (use & 1) ^ 1)) { ok = false; fail_it = it; break; }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       const bool real = cur.w >= 0 && cur.s >= 0;
-      if (real && !mbar_wait(&plbar[buf], use & 1)) { ok = false; break; }
+      if (real && !mbar_wait(&plbar[buf], use & 1)) { ok = false; fail_it = it; break; }
       const PipeLayout& P = a.L[cur.l];
       const int tile = cur.w >= 0 ? cur.wl / P.nblocks : 0;
       const unsigned char* xt = P.xs + (size_t)tile * P.ncols * C::PIXB;
@@ -312,7 +311,6 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
         *hbuf(buf) = h;
       }
       if (real) {
-        if (buf) issued1 = (int)use; else issued0 = (int)use;
         // staged rows: PL lanes per row; instruction j copies bytes
         // [16 PL j, 16 PL (j+1)) of RPI rows
         constexpr int PL = C::PL;
@@ -353,9 +351,12 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
     }
     if (!ok) {
       if (lane == 0) atomicExch(a.err, 1);
-      // let copies already issued land before the CTA's shared memory goes away
-      if (issued0 >= 0) mbar_wait(&full[0], (uint32_t)issued0 & 1);
-      if (issued1 >= 0) mbar_wait(&full[1], (uint32_t)issued1 & 1);
+      // let copies already issued land before the CTA's shared memory goes
+      // away: the last NB iterations before the failing one completed their
+      // arrivals on the full barriers (every iteration arrives, with copies
+      // or without)
+      for (uint32_t j = fail_it > (uint32_t)NB ? fail_it - NB : 0; j < fail_it; ++j)
+        mbar_wait(&full[j % NB], (j / NB) & 1);
     }
     return;
   }
@@ -368,8 +369,8 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
 #pragma unroll
   for (int i = 0; i < C::SPL; ++i) acc[i] = 0.0f;
   for (uint32_t it = 0;; ++it) {
-    const int buf = it & 1;
-    if (!mbar_wait(&full[buf], (it >> 1) & 1)) {
+    const int buf = (int)(it % kPipeBufs);
+    if (!mbar_wait(&full[buf], (it / kPipeBufs) & 1)) {
       if (lane == 0) atomicExch(a.err, 1);
       return;
     }
@@ -508,7 +509,7 @@ size_t pipe_smem_bytes(int cap, int64_t emax, int pixb, int eb, uint32_t* xbytes
   const size_t list = ((size_t)cap * 4 + 127) / 128 * 128;
   if (xbytes) *xbytes = (uint32_t)x;
   if (ebytes) *ebytes = (uint32_t)e;
-  return 2 * (x + e + 256 + 128) + 2 * list + 64;
+  return kPipeBufs * (x + e + 256 + 128) + kPipeBufs * list + 128;
 }
 
 // shared memory a pipeline CTA may use so that kPipeCtasPerSm fit on an SM

@@ -115,9 +115,20 @@ inline size_t pipe_buffer_bytes(const Layout& L, int pixb) {
   return x + e + list + 128 * 2 + 256;
 }
 constexpr int kPipeCtasPerSm = 2;
-// shared memory one pipeline CTA may use for its two buffers (the rest of its
+#ifndef XCT_PIPE_BUFS
+#define XCT_PIPE_BUFS 2
+#endif
+// stage buffers of a pipeline CTA (the producer fills up to kPipeBufs - 1
+// stages ahead of the consumers)
+constexpr int kPipeBufs = XCT_PIPE_BUFS;
+static_assert(kPipeBufs == 2 || kPipeBufs == 3, "pipeline buffers");
+// shared memory one pipeline CTA may use for its buffers (the rest of its
 // 113 KB share goes to the barriers)
 constexpr size_t kPipeSmemLimit = 110 * 1024;
+// first stage capacity tried for each entry size (reduced until the buffers
+// fit in kPipeSmemLimit)
+constexpr int kPipeCap16 = kPipeBufs == 2 ? 280 : 184;
+constexpr int kPipeCap32 = kPipeBufs == 2 ? 200 : 132;
 
 struct Plan {
   xct_geometry g{};

@@ -128,17 +128,33 @@ def test_hilbert_curve_is_adjacent_walk(side):
     assert pos[0] == (0, 0) and pos[side * side - 1] == (side - 1, 0)
 
 
-@pytest.mark.parametrize("nx,ny,tile", [(16, 16, 8), (13, 7, 4), (128, 180, 8), (5, 5, 8), (1, 1, 8)])
-def test_hilbert_order_tiles(nx, ny, tile):
-    perm = oracle.hilbert_order(nx, ny, tile)
+@pytest.mark.parametrize("inner", ["row", "col", "quad"])
+@pytest.mark.parametrize("nx,ny,tile", [(16, 16, 8), (13, 7, 4), (128, 180, 8), (5, 5, 8), (1, 1, 8),
+                                        (10, 6, 4)])
+def test_hilbert_order_tiles(nx, ny, tile, inner):
+    perm = oracle.hilbert_order(nx, ny, tile, inner)
     assert sorted(perm.tolist()) == list(range(nx * ny))
     grid = perm.reshape(ny, nx)
-    # every tile holds a contiguous id range, row-major inside
+    # every tile holds a contiguous id range, numbered as `inner` says
     for ty in range(0, ny, tile):
         for tx in range(0, nx, tile):
             blk = grid[ty:ty + tile, tx:tx + tile]
-            flat = blk.reshape(-1)
-            assert np.array_equal(flat, flat[0] + np.arange(flat.size))
+            h, w = blk.shape
+            rel = blk - blk.min()
+            assert sorted(rel.reshape(-1).tolist()) == list(range(h * w))
+            if inner == "row" or (inner == "quad" and (h % 2 or w % 2)):
+                assert np.array_equal(rel, np.arange(h * w).reshape(h, w))
+            elif inner == "col":
+                assert np.array_equal(rel, np.arange(h * w).reshape(w, h).T)
+            else:
+                # ids 4k..4k+3 fill one 2 x 2 square, row-major inside it;
+                # the squares themselves row-major
+                for k in range(h * w // 4):
+                    ys, xs = np.nonzero((rel >= 4 * k) & (rel < 4 * k + 4))
+                    y0, x0 = ys.min(), xs.min()
+                    assert y0 % 2 == 0 and x0 % 2 == 0
+                    assert np.array_equal(rel[y0:y0 + 2, x0:x0 + 2], 4 * k + np.array([[0, 1], [2, 3]]))
+                    assert k == (y0 // 2) * (w // 2) + x0 // 2
     # first tile is the one at the origin
     assert grid[0, 0] == 0
 
