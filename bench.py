@@ -297,21 +297,31 @@ def run_ours(args):
     # per-launch duration from CUDA events on its stream
     flops_launch = 2.0 * nnz * S
     achieved = flops_launch / (proj16 * 1e-3) / 1e12
-    alu_peak = 128 * 2 * nsm * sm_mhz * 1e6 / 1e12
+    clk = sm_mhz * 1e6
+    # three roofs of the 16-bit product (per launch):
+    #  FP32 FMA pipe: nsm x 128 FMA/clk x 2 flop
+    #  16-bit operands: every FMA also issues one 16->32-bit conversion, and
+    #    reads 2 bytes of a staged row from shared memory (128 B/clk/SM):
+    #    both give nsm x 64 FMA/clk x 2 flop
+    #  HBM: 2 flop per matrix entry and slice over the algorithmic bytes
+    fma_peak = 128 * 2 * nsm * clk / 1e12
+    op16_peak = 64 * 2 * nsm * clk / 1e12
     rows_a, cols_a = m * nd, n * n
-    alg_bytes = nnz * 4 + (rows_a + 1) * 8 + S * cols_a * 4 + S * rows_a * 4
-    alg_bytes_bp = nnz * 4 + (cols_a + 1) * 8 + S * rows_a * 4 + S * cols_a * 4
+    alg_bytes = nnz * 4 + (rows_a + 1) * 8 + S * cols_a * 2 + S * rows_a * 4
+    alg_bytes_bp = nnz * 4 + (cols_a + 1) * 8 + S * rows_a * 2 + S * cols_a * 4
+    hbm_roof = flops_launch / (alg_bytes / (peak_hbm * 1e9)) / 1e12
     gather_bytes = nnz * S * 2
-    smem_peak = 128.0 * nsm * sm_mhz * 1e6 / 1e9
+    smem_peak = 128.0 * nsm * clk / 1e9
     traffic = _profiled_traffic("spmm_pipe_f16_projection")
     value = flops_step / (ms16 * 1e-3) / 1e9
+    peak = min(fma_peak, op16_peak, hbm_roof)
     out = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms16,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
         "data": "synthetic (seeded ellipsoid phantom, exact line integrals, Poisson 1e4)",
         "config": {"workload": WORKLOAD, "n": n, "angles": m, "bins": nd, "slices_per_gpu": S,
-                   "iters": K, "nnz": nnz, "l2": "inputs larger than L2 (packed A 1.3 GB per product)",
+                   "iters": K, "nnz": nnz, "l2": "inputs larger than L2 (packed A 1.2 GB per product)",
                    "parallelism": f"slice-sharded x{world}, no collective"},
         "fp32": {"value": flops_step / (ms32 * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms32,
                  "cgls_iter_per_s": K / (ms32 * 1e-3)},
@@ -323,17 +333,22 @@ def run_ours(args):
         "kernel_ms": {"project_f16": proj16, "backproject_f16": back16, "other_f16_per_step": other16,
                       "project_f32": proj32, "backproject_f32": back32, "other_f32_per_step": other32},
         "roofline": {
-            "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-            "frac": achieved / alu_peak, "traffic": traffic,
+            "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic,
             "kernel": "spmm_pipe_kernel<__half,64> (projection, 2*nnz*S flops per launch)",
-            "peak_source": f"derived: {nsm} SMs x 128 FP32 FMA/clk x 2 flop x {sm_mhz:.0f} MHz "
-                           "(median SM clock during the timed region)",
+            "peak_source": (f"derived, the least of three roofs at the median SM clock {sm_mhz:.0f} MHz: "
+                            f"16-bit operand roof {op16_peak:.1f} (one conversion per FMA issued beside "
+                            f"it, {nsm} SMs x 64 FMA/clk x 2 flop; equal to the shared-memory gather "
+                            f"roof at 2 B per FMA), FP32 FMA roof {fma_peak:.1f} ({nsm} x 128 FMA/clk x "
+                            f"2 flop), HBM roof {hbm_roof:.1f} (2*nnz*S flop over the algorithmic bytes "
+                            f"at the measured {peak_hbm:.0f} GB/s)"),
+            "fp32_fma": {"peak": fma_peak, "frac": achieved / fma_peak},
             "hbm": {"achieved_gbs": alg_bytes / (proj16 * 1e-3) / 1e9, "peak_gbs": peak_hbm,
                     "frac": alg_bytes / (proj16 * 1e-3) / 1e9 / peak_hbm, "peak_source": peak_kind,
-                    "alg_bytes_per_launch": alg_bytes},
+                    "alg_bytes_per_launch": alg_bytes,
+                    "traffic_over_alg": (traffic / alg_bytes) if traffic else None},
             "smem_gather": {"achieved_gbs": gather_bytes / (proj16 * 1e-3) / 1e9, "peak_gbs": smem_peak,
-                            "frac": gather_bytes / (proj16 * 1e-3) / 1e9 / smem_peak,
-                            "peak_source": f"derived: {nsm} SMs x 128 B/clk x {sm_mhz:.0f} MHz"},
+                            "frac": gather_bytes / (proj16 * 1e-3) / 1e9 / smem_peak},
         },
         "clocks": clocks,
         "gpu_launches": launches,
