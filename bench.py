@@ -287,6 +287,18 @@ def run_ours(args):
     e2e_ms = shard.max_over_ranks((time.perf_counter() - e0) / e2e_steps * 1e3, dev)
 
     rel = float(torch.linalg.norm(xs["f16"] - xs["f32"]) / torch.linalg.norm(xs["f32"]))
+    # residual curves of the two solves (||y - A x_k|| per slice and
+    # iteration, as the solver logs them) and the error of one mixed
+    # projection against the FP32 one, on the FP32 iterate
+    logs = {}
+    for kind in plans:
+        lg = torch.zeros((K + 1, S, 2), dtype=torch.float64, device=dev)
+        xct.xct_cgls(plans[kind].handle, y, xs[kind], S, K, 0, lg, stream)
+        logs[kind] = lg[:, :, 0]
+    track = (logs["f16"] / logs["f32"] - 1.0).abs()
+    q16, q32 = plans["f16"].project(xs["f32"]), plans["f32"].project(xs["f32"])
+    proj_err = float(torch.linalg.norm((q16 - q32).double()) / torch.linalg.norm(q32.double()))
+    track_max, track_final = float(track.max()), float(track[-1].max())
 
     if rank != 0:
         return
@@ -329,6 +341,8 @@ def run_ours(args):
         "cgls_iter_per_s": K / (ms16 * 1e-3),
         "hbm_gbs_alg": (alg_bytes * K + alg_bytes_bp * (K + 1)) / (ms16 * 1e-3) / 1e9,
         "rel_err_mixed_vs_fp32": rel,
+        "residual_curve_mixed_vs_fp32": {"max_rel_dev": track_max, "final_rel_dev": track_final},
+        "rel_err_projection_mixed_vs_fp32": proj_err,
         "graph_ms_per_step": graph_ms,
         "kernel_ms": {"project_f16": proj16, "backproject_f16": back16, "other_f16_per_step": other16,
                       "project_f32": proj32, "backproject_f32": back32, "other_f32_per_step": other32},

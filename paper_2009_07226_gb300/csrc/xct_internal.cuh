@@ -79,7 +79,6 @@ struct Arena {
 
 constexpr int kRowsPerBlock = 64;              // rows of one thread block
 constexpr int kQuads = kRowsPerBlock / 4;      // 4-row groups per block
-constexpr int kDefaultCapacity = 848;          // staged vectors per stage
 
 // One (stage, quad) segment: the entries of 4 consecutive rows interleaved in
 // chunks of 4 entries; `off` counts entries from the start of `ent`.
