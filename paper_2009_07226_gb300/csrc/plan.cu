@@ -607,6 +607,43 @@ __global__ void stage_pix_kernel(const int64_t* blk_stage, const int64_t* fp_off
     stage_pix[s] = fp_off[b] + (s - blk_stage[b]) * cap;
 }
 
+// Contiguous runs of each stage's staged rows, for one bulk copy per run:
+// pairs (first row id, first position in the stage), then a closing pair
+// (-1, rows of the stage) repeated to an even count (16-byte aligned lists).
+// One thread per block walks the block's stages.
+__global__ void run_count_kernel(const int64_t* blk_stage, const int64_t* fp_off,
+                                 const int64_t* fp_size, const int32_t* pix, int32_t nblocks,
+                                 int32_t cap, int64_t* nrun, unsigned long long* rmax) {
+  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= nblocks) return;
+  for (int64_t s = blk_stage[b]; s < blk_stage[b + 1]; ++s) {
+    const int64_t k = s - blk_stage[b];
+    const int64_t p0 = fp_off[b] + k * cap;
+    const int64_t n = min((int64_t)cap, fp_size[b] - k * cap);
+    int64_t r = 0;
+    for (int64_t i = 0; i < n; ++i)
+      if (i == 0 || pix[p0 + i] != pix[p0 + i - 1] + 1) ++r;
+    nrun[s] = (r + 2) & ~(int64_t)1;
+    atomicMax(rmax, (unsigned long long)nrun[s]);
+  }
+}
+
+__global__ void run_fill_kernel(const int64_t* blk_stage, const int64_t* fp_off,
+                                const int64_t* fp_size, const int32_t* pix, int32_t nblocks,
+                                int32_t cap, const int64_t* run_off, int2* runs) {
+  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= nblocks) return;
+  for (int64_t s = blk_stage[b]; s < blk_stage[b + 1]; ++s) {
+    const int64_t k = s - blk_stage[b];
+    const int64_t p0 = fp_off[b] + k * cap;
+    const int n = (int)min((int64_t)cap, fp_size[b] - k * cap);
+    int64_t o = run_off[s];
+    for (int i = 0; i < n; ++i)
+      if (i == 0 || pix[p0 + i] != pix[p0 + i - 1] + 1) runs[o++] = make_int2(pix[p0 + i], i);
+    for (; o < run_off[s + 1]; ++o) runs[o] = make_int2(-1, n);
+  }
+}
+
 // per (stage, quad): the 4 row counts and the padded slot count
 __global__ void __launch_bounds__(kRowsPerBlock) seg_count_kernel(CsrView m, const int32_t* epos,
                                                                   const int64_t* blk_stage,
@@ -766,6 +803,34 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
   XCT_TRY(tmp.get(&slot_off, L.nstages * kQuads + 1));
   stage_pix_kernel<<<grid_for(nb + 1, 256), 256, 0, s>>>(L.blk_stage, fp_off, nb, cap, L.stage_pix);
   count_launch();
+  {
+    int64_t* nrun;
+    unsigned long long* rmax;
+    XCT_TRY(tmp.get(&nrun, L.nstages));
+    XCT_TRY(tmp.get(&rmax, 1));
+    XCT_TRY(own.get(&L.stage_run, L.nstages + 1));
+    XCT_TRY_CUDA(cudaMemsetAsync(rmax, 0, sizeof(unsigned long long), s));
+    if (nb > 0) {
+      run_count_kernel<<<grid_for(nb, 128), 128, 0, s>>>(L.blk_stage, fp_off, fp_size, L.pix, nb, cap,
+                                                         nrun, rmax);
+      count_launch();
+    }
+    XCT_TRY(exclusive_scan_i64(nrun, L.stage_run, L.nstages, s));
+    int64_t nruns = 0;
+    unsigned long long rmax_h = 0;
+    XCT_TRY_CUDA(cudaMemcpyAsync(&nruns, L.stage_run + L.nstages, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, s));
+    XCT_TRY_CUDA(cudaMemcpyAsync(&rmax_h, rmax, sizeof(rmax_h), cudaMemcpyDeviceToHost, s));
+    XCT_TRY_CUDA(cudaStreamSynchronize(s));
+    L.nruns = nruns;
+    L.run_max = (int64_t)rmax_h;
+    XCT_TRY(own.get(&L.runs, nruns));
+    if (nb > 0) {
+      run_fill_kernel<<<grid_for(nb, 128), 128, 0, s>>>(L.blk_stage, fp_off, fp_size, L.pix, nb, cap,
+                                                        L.stage_run, L.runs);
+      count_launch();
+    }
+  }
   if (nb > 0) {
     seg_count_kernel<<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, slots);
     count_launch();
@@ -812,7 +877,7 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
   XCT_TRY_CUDA(cudaGetLastError());
   XCT_TRY_CUDA(cudaStreamSynchronize(s));
   L.bytes = (int64_t)L.nslots * L.ebytes + L.nstages * (int64_t)sizeof(Seg) +
-            (L.nstages + 1) * 16 + (int64_t)(nb + 1) * 8 + total_fp * 4;
+            (L.nstages + 1) * 24 + (int64_t)(nb + 1) * 8 + total_fp * 4 + L.nruns * 8;
   own.move_to(keep);
   return XCT_OK;
 }

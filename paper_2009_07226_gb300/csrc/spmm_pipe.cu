@@ -4,15 +4,16 @@
 //
 // Two CTAs per SM.  A producer warp takes blocks of 64 rows from a work
 // counter and streams each stage of each block into one of two shared-memory
-// buffers: the stage's staged input rows are gathered with 16-byte cp.async
-// copies (one or two lanes per 128-byte row, from a row-id list fetched one
-// stage ahead by a bulk copy), its packed entries and segment headers arrive
-// as two bulk copies (cp.async.bulk) counted in bytes on the same mbarrier.
-// Sixteen consumer warps compute from shared memory only and release the
-// buffer through a second mbarrier; while they work on one stage the next one
-// (possibly of the next block) is already in flight.  The lane layout of the
-// consumers is the one of spmm.cu: a group of lanes holds different slices of
-// one row, so every shared-memory wavefront reads one contiguous staged row.
+// buffers with bulk asynchronous copies (cp.async.bulk) counted in bytes on
+// the buffer's mbarrier: one copy per contiguous run of the stage's staged
+// input rows (runs of consecutive Hilbert ids, about 11 rows on average; the
+// run list itself arrives one stage ahead by another bulk copy), one for the
+// stage's packed entries and one for its segment headers.  Sixteen consumer
+// warps compute from shared memory only and release the buffer through a
+// second mbarrier; while they work on one stage the next one (possibly of the
+// next block) is already in flight.  The lane layout of the consumers is the
+// one of spmm.cu: a group of lanes holds different slices of one row, so every
+// shared-memory wavefront reads one contiguous staged row.
 //
 // Every wait is bounded (about two seconds of wall time); a wait that runs out
 // sets the caller's error flag, waits (bounded) for the copies this CTA has in
@@ -41,10 +42,6 @@ struct PCfg {
   static constexpr int NT = (NC + 1) * 32;         // + one producer warp
   static constexpr bool E16 = XB == 2;
   static constexpr int EB = E16 ? 4 : 8;           // bytes per packed entry
-  // producer lanes per staged row: each lane copies PIXB / PL bytes of its
-  // row (fewer lanes per row: fewer producer instructions per stage; measured
-  // best at one lane per row for 16-bit rows, two for FP32 rows)
-  static constexpr int PL = E16 ? 1 : 2;
 };
 
 struct __align__(16) Hdr {
@@ -59,9 +56,9 @@ struct __align__(16) Hdr {
 // One product of a launch: a layout with its input / output vectors.
 struct PipeLayout {
   const int64_t* blk_stage;
-  const int64_t* stage_pix;
+  const int64_t* stage_run;
   const int64_t* stage_ent;
-  const int32_t* pix;
+  const int2* runs;
   const Seg* seg;
   const unsigned char* ent;
   int64_t nrows, ncols;
@@ -79,6 +76,7 @@ struct PipeArgs {
   int nl;                    // products in this launch
   int nwork;                 // work items over all products
   int cap;                   // largest stage capacity (buffer rows)
+  uint32_t listbytes;        // per-slot run-list region (128-byte multiple)
   int* work;
   int* err;
   uint32_t xbytes, ebytes;   // per-buffer region sizes (128-byte multiples)
@@ -92,6 +90,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_arrive_tx(uint64_t* bar, uint32_t tx) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bar)), "r"(tx)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t tx) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(su32(bar)), "r"(tx)
                : "memory");
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -127,20 +129,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
           su32(dst)),
       "l"(src), "r"(bytes), "r"(su32(bar))
       : "memory");
-}
-
-__device__ __forceinline__ void cp16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(dst)), "l"(src) : "memory");
-}
-// 16-byte copy at a constant byte offset from both addresses
-template <int OFF>
-__device__ __forceinline__ void cp16_at(uint32_t dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0+%2], [%1+%2], 16;" ::"r"(dst), "l"(src), "n"(OFF)
-               : "memory");
-}
-// arrive on `bar` once every cp.async this thread issued so far has landed
-__device__ __forceinline__ void cp_arrive_noinc(uint64_t* bar) {
-  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(su32(bar)) : "memory");
 }
 
 // mixed-precision FMA of one staged 16-byte vector (see spmm.cu)
@@ -190,13 +178,13 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
   using C = PCfg<TX, ST>;
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t bufbytes = a.xbytes + a.ebytes + 256 + 128;
-  const uint32_t listbytes = (uint32_t)(((size_t)a.cap * 4 + 127) / 128 * 128);
+  const uint32_t listbytes = a.listbytes;
   constexpr int NB = kPipeBufs;
-  int32_t* lists = reinterpret_cast<int32_t*>(smem + NB * bufbytes);
+  int2* lists = reinterpret_cast<int2*>(smem + NB * bufbytes);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NB * bufbytes + NB * listbytes);
   uint64_t* empty = full + NB;
-  uint64_t* plbar = full + 2 * NB;   // row-id list of a stage landed
-  auto plist = [&](int slot) { return lists + (size_t)slot * (listbytes / 4); };
+  uint64_t* plbar = full + 2 * NB;   // run list of a stage landed
+  auto plist = [&](int slot) { return lists + (size_t)slot * (listbytes / 8); };
   auto xbuf = [&](int b) { return smem + b * bufbytes; };
   auto ebuf = [&](int b) { return smem + b * bufbytes + a.xbytes; };
   auto sbuf = [&](int b) { return smem + b * bufbytes + a.xbytes + a.ebytes; };
@@ -205,7 +193,7 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int b = 0; b < NB; ++b) {
-      mbar_init(&full[b], 33);
+      mbar_init(&full[b], 1);
       mbar_init(&empty[b], C::NC);
       mbar_init(&plbar[b], 1);
     }
@@ -230,16 +218,17 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
     struct Ref {
       int w, l, wl, k, nst;
       int64_t s;
-      int64_t p0, e0;
-      int np;
+      int64_t r0, e0;
+      int nr, np;
       uint32_t eb;
     };
     auto meta = [&](Ref& r) {
-      r.p0 = 0; r.e0 = 0; r.np = 0; r.eb = 0;
+      r.r0 = 0; r.e0 = 0; r.nr = 0; r.np = 0; r.eb = 0;
       if (r.w >= 0 && r.s >= 0) {
         const PipeLayout& P = a.L[r.l];
-        r.p0 = P.stage_pix[r.s];
-        r.np = (int)(P.stage_pix[r.s + 1] - r.p0);
+        r.r0 = P.stage_run[r.s];
+        r.nr = (int)(P.stage_run[r.s + 1] - r.r0);
+        r.np = P.runs[r.r0 + r.nr - 1].y;   // the closing pair holds the row count
         r.e0 = P.stage_ent[r.s];
         r.eb = (uint32_t)((P.stage_ent[r.s + 1] - r.e0) * C::EB);
       }
@@ -248,7 +237,7 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
       int w = 0;
       if (lane == 0) w = atomicAdd(a.work, 1);
       w = __shfl_sync(0xffffffffu, w, 0);
-      Ref r{-1, 0, 0, 0, 1, -1, 0, 0, 0, 0u};
+      Ref r{-1, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0u};
       if (w >= nwork) return r;
       int l = a.nl - 1;
       while (l > 0 && w < a.L[l].work_begin) --l;
@@ -256,18 +245,17 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
       const int wl = w - P.work_begin;
       const int b = wl % P.nblocks;
       const int64_t s0 = P.blk_stage[b], s1 = P.blk_stage[b + 1];
-      r = Ref{w, l, wl, 0, s1 > s0 ? (int)(s1 - s0) : 1, s1 > s0 ? s0 : (int64_t)-1, 0, 0, 0, 0u};
+      r = Ref{w, l, wl, 0, s1 > s0 ? (int)(s1 - s0) : 1, s1 > s0 ? s0 : (int64_t)-1, 0, 0, 0, 0, 0u};
       meta(r);
       return r;
     };
-    // the row-id list of stage r into list slot `slot` (one bulk copy; the
-    // lists are 16-byte aligned and padded to 4 ids)
+    // the run list of stage r into list slot `slot` (one bulk copy; lists
+    // hold an even number of 8-byte pairs, so 16-byte multiples)
     auto request = [&](const Ref& r, int slot) {
       if (lane != 0) return;
       if (r.w >= 0 && r.s >= 0) {
-        const uint32_t n4 = (uint32_t)((r.np + 3) & ~3);
-        mbar_arrive_tx(&plbar[slot], n4 * 4u);
-        bulk_g2s(plist(slot), a.L[r.l].pix + r.p0, n4 * 4u, &plbar[slot]);
+        mbar_arrive_tx(&plbar[slot], (uint32_t)r.nr * 8u);
+        bulk_g2s(plist(slot), a.L[r.l].runs + r.r0, (uint32_t)r.nr * 8u, &plbar[slot]);
       } else {
         mbar_arrive(&plbar[slot]);
       }
@@ -279,10 +267,10 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
     for (uint32_t it = 0;; ++it) {
       const int buf = (int)(it % NB);
       const uint32_t use = it / NB;
-      Ref nxt{-1, 0, 0, 0, 1, -1, 0, 0, 0, 0u};
+      Ref nxt{-1, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0u};
       if (cur.w >= 0) {
         if (cur.k + 1 < cur.nst) {
-          nxt = Ref{cur.w, cur.l, cur.wl, cur.k + 1, cur.nst, cur.s >= 0 ? cur.s + 1 : -1, 0, 0, 0, 0u};
+          nxt = Ref{cur.w, cur.l, cur.wl, cur.k + 1, cur.nst, cur.s >= 0 ? cur.s + 1 : -1, 0, 0, 0, 0, 0u};
           meta(nxt);
         } else {
           nxt = fetch();
@@ -311,41 +299,30 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
         *hbuf(buf) = h;
       }
       if (real) {
-        // staged rows: PL lanes per row; instruction j copies bytes
-        // [16 PL j, 16 PL (j+1)) of RPI rows
-        constexpr int PL = C::PL;
-        constexpr int RPI = 32 / PL;
-        const int pr = lane / PL, pc = lane % PL;
-        const uint32_t xd = su32(xbuf(buf)) + (uint32_t)(pr * C::PIXB + pc * 16);
-        const int32_t* pl = plist(buf);
-        const unsigned char* xs0 = xt + pc * 16;
-        for (int r = pr; r < np; r += RPI) {
-          const unsigned char* src = xs0 + (size_t)pl[r] * C::PIXB;
-          const uint32_t dst = xd + (uint32_t)((r - pr) * C::PIXB);
-          cp16_at<0>(dst, src);
-          if constexpr (C::PIXB > PL * 16) cp16_at<PL * 16>(dst, src);
-          if constexpr (C::PIXB > 2 * PL * 16) cp16_at<2 * PL * 16>(dst, src);
-          if constexpr (C::PIXB > 3 * PL * 16) cp16_at<3 * PL * 16>(dst, src);
-          if constexpr (C::PIXB > 4 * PL * 16) {
-            cp16_at<4 * PL * 16>(dst, src);
-            cp16_at<5 * PL * 16>(dst, src);
-            cp16_at<6 * PL * 16>(dst, src);
-            cp16_at<7 * PL * 16>(dst, src);
+        // one bulk copy per contiguous run of staged rows, plus the stage's
+        // packed entries and segment headers, all counted in bytes on the
+        // full barrier (the expected count is set before any copy starts)
+        if (lane == 0)
+          mbar_expect_tx(&full[buf], (uint32_t)np * C::PIXB + eb + 256u);
+        __syncwarp();
+        const int2* rl = plist(buf);
+        unsigned char* xd = xbuf(buf);
+        for (int k = lane; k < cur.nr; k += 32) {
+          const int2 run = rl[k];
+          if (run.x >= 0) {
+            const uint32_t len = (uint32_t)(rl[k + 1].y - run.y);
+            bulk_g2s(xd + (size_t)run.y * C::PIXB, xt + (size_t)run.x * C::PIXB, len * C::PIXB,
+                     &full[buf]);
           }
         }
-      }
-      cp_arrive_noinc(&full[buf]);
-      if (lane == 0) {
-        // the stage's packed entries and segment headers: two bulk copies
-        // counted in bytes; this arrival also publishes the header
-        if (real) {
-          mbar_arrive_tx(&full[buf], eb + 256u);
+        if (lane == 0) {
           if (eb) bulk_g2s(ebuf(buf), P.ent + (size_t)cur.e0 * C::EB, eb, &full[buf]);
           bulk_g2s(sbuf(buf), P.seg + cur.s * kQuads, 256u, &full[buf]);
-        } else {
-          mbar_arrive(&full[buf]);
         }
       }
+      // the single arrival of this phase; it also publishes the header
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[buf]);
       if (cur.w < 0) break;
       cur = nxt;
     }
@@ -503,12 +480,14 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_ke
   }
 }
 
-size_t pipe_smem_bytes(int cap, int64_t emax, int pixb, int eb, uint32_t* xbytes, uint32_t* ebytes) {
+size_t pipe_smem_bytes(int cap, int64_t emax, int64_t rmax, int pixb, int eb, uint32_t* xbytes,
+                       uint32_t* ebytes, uint32_t* lbytes) {
   const size_t x = ((size_t)(cap + 1) * pixb + 127) / 128 * 128;
   const size_t e = ((size_t)emax * eb + 127) / 128 * 128;
-  const size_t list = ((size_t)cap * 4 + 127) / 128 * 128;
+  const size_t list = ((size_t)rmax * 8 + 127) / 128 * 128;
   if (xbytes) *xbytes = (uint32_t)x;
   if (ebytes) *ebytes = (uint32_t)e;
+  if (lbytes) *lbytes = (uint32_t)list;
   return kPipeBufs * (x + e + 256 + 128) + kPipeBufs * list + 128;
 }
 
@@ -527,15 +506,15 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   }
   PipeArgs a{};
   int work = 0, cap = 0;
-  int64_t emax = 0;
+  int64_t emax = 0, rmax = 0;
   for (int i = 0; i < count; ++i) {
     const SpmmArgs& s = list[i];
     const Layout& L = *s.L;
     PipeLayout& P = a.L[i];
     P.blk_stage = L.blk_stage;
-    P.stage_pix = L.stage_pix;
+    P.stage_run = L.stage_run;
     P.stage_ent = L.stage_ent;
-    P.pix = L.pix;
+    P.runs = L.runs;
     P.seg = L.seg;
     P.ent = static_cast<const unsigned char*>(L.ent);
     P.nrows = L.nrows;
@@ -553,13 +532,15 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
     work += L.nblocks * s.ntiles;
     cap = cap > L.cap ? cap : L.cap;
     emax = emax > L.emax_slots ? emax : L.emax_slots;
+    rmax = rmax > L.run_max ? rmax : L.run_max;
   }
   a.nl = count;
   a.nwork = work;
   a.cap = cap;
   a.work = list[0].work;
   a.err = list[0].err;
-  const size_t smem = pipe_smem_bytes(cap, emax, C::PIXB, C::EB, &a.xbytes, &a.ebytes);
+  const size_t smem = pipe_smem_bytes(cap, emax, rmax, C::PIXB, C::EB, &a.xbytes, &a.ebytes,
+                                      &a.listbytes);
   if (smem > kPipeCtaSmemMax) {
     set_error("persistent product: %zu bytes of shared memory needed", smem);
     return XCT_ERR_UNSUPPORTED;
@@ -614,8 +595,8 @@ bool spmm_pipe_applies(const SpmmArgs& a) {
   const int pixb = a.st * (a.storage == XCT_F32 ? 4 : 2);
   if (pixb != 128 || !a.work || !a.err) return false;
   if (a.L->nblocks == 0) return false;
-  return pipe_smem_bytes(a.L->cap, a.L->emax_slots, 128, a.storage == XCT_F32 ? 8 : 4, nullptr,
-                         nullptr) <= kPipeCtaSmemMax;
+  return pipe_smem_bytes(a.L->cap, a.L->emax_slots, a.L->run_max, 128,
+                         a.storage == XCT_F32 ? 8 : 4, nullptr, nullptr, nullptr) <= kPipeCtaSmemMax;
 }
 
 xct_status spmm_pipe(const SpmmArgs& a, cudaStream_t s) { return pipe_any(&a, 1, s); }
@@ -623,14 +604,15 @@ xct_status spmm_pipe(const SpmmArgs& a, cudaStream_t s) { return pipe_any(&a, 1,
 bool spmm_pipe_multi_applies(const SpmmArgs* list, int count) {
   if (count < 1 || count > kMaxPipeProducts) return false;
   int cap = 0;
-  int64_t emax = 0;
+  int64_t emax = 0, rmax = 0;
   for (int i = 0; i < count; ++i) {
     if (!spmm_pipe_applies(list[i]) || list[i].storage != list[0].storage) return false;
     cap = cap > list[i].L->cap ? cap : list[i].L->cap;
     emax = emax > list[i].L->emax_slots ? emax : list[i].L->emax_slots;
+    rmax = rmax > list[i].L->run_max ? rmax : list[i].L->run_max;
   }
-  return pipe_smem_bytes(cap, emax, 128, list[0].storage == XCT_F32 ? 8 : 4, nullptr, nullptr) <=
-         kPipeCtaSmemMax;
+  return pipe_smem_bytes(cap, emax, rmax, 128, list[0].storage == XCT_F32 ? 8 : 4, nullptr, nullptr,
+                         nullptr) <= kPipeCtaSmemMax;
 }
 
 xct_status spmm_pipe_multi(const SpmmArgs* list, int count, cudaStream_t s) {

@@ -102,6 +102,11 @@ struct Layout {
   void* ent = nullptr;            // packed entries
   int64_t* stage_ent = nullptr;   // [nstages + 1] first slot of each stage's entries
   int64_t emax_slots = 0;         // largest stage, in slots
+  // contiguous runs of each stage's staged rows (see run_fill_kernel)
+  int64_t* stage_run = nullptr;   // [nstages + 1] offsets into runs (even)
+  int2* runs = nullptr;           // (first row id, first position) pairs
+  int64_t nruns = 0;              // pairs over all stages
+  int64_t run_max = 0;            // largest stage list, in pairs
   int64_t bytes = 0;
 };
 
@@ -110,7 +115,7 @@ struct Layout {
 inline size_t pipe_buffer_bytes(const Layout& L, int pixb) {
   size_t x = ((size_t)(L.cap + 1) * pixb + 127) / 128 * 128;
   size_t e = ((size_t)L.emax_slots * L.ebytes + 127) / 128 * 128;
-  size_t list = ((size_t)L.cap * 4 + 127) / 128 * 128;
+  size_t list = ((size_t)L.run_max * 8 + 127) / 128 * 128;
   return x + e + list + 128 * 2 + 256;
 }
 constexpr int kPipeCtasPerSm = 2;
