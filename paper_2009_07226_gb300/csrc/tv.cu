@@ -10,6 +10,7 @@
 //   -(dx + dy)/mag at (i, j),  dx/mag at (i, j-1),  dy/mag at (i-1, j).
 #include <math.h>
 
+#include "ff.cuh"
 #include "xct_internal.cuh"
 
 namespace xct {
@@ -29,11 +30,12 @@ __device__ __forceinline__ TvTerm tv_term(const float* xs, int n, int i, int j, 
   return TvTerm{dx, dy, sqrtf(dx * dx + dy * dy + eps2)};
 }
 
-// grid (tiles_x * tiles_y, S); partial[s][tile] = sum of magnitudes (FP64)
+// grid (tiles_x * tiles_y, S); partial[s][tile] = sum of magnitudes (FP64
+// value of an FP32-pair sum)
 __global__ void __launch_bounds__(kTvThreads) tv_kernel(const float* __restrict__ x, int n, float eps,
                                                         float weight, float* __restrict__ grad,
                                                         int accumulate, double* __restrict__ partial) {
-  __shared__ double red[kTvThreads / 32];
+  __shared__ FF red[kTvThreads / 32];
   const int s = blockIdx.y;
   const int tiles_x = (n + kTvTile - 1) / kTvTile;
   const int ti = blockIdx.x / tiles_x, tj = blockIdx.x % tiles_x;
@@ -41,10 +43,10 @@ __global__ void __launch_bounds__(kTvThreads) tv_kernel(const float* __restrict_
   const int j = tj * kTvTile + threadIdx.x % kTvTile;
   const float* xs = x + (size_t)s * n * n;
   const float eps2 = eps * eps;
-  double val = 0.0;
+  FF val{0.0f, 0.0f};
   if (i < n && j < n) {
     const TvTerm t = tv_term(xs, n, i, j, eps2);
-    val = (double)t.mag;
+    val.hi = t.mag;
     float g = -(t.dx + t.dy) / t.mag;
     if (j > 0) {
       const TvTerm l = tv_term(xs, n, i, j - 1, eps2);
@@ -59,13 +61,14 @@ __global__ void __launch_bounds__(kTvThreads) tv_kernel(const float* __restrict_
       *gp = accumulate ? *gp + weight * g : weight * g;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+  // block sum in FP32 pairs (ff.cuh), one FP64 partial per block
+  for (int o = 16; o > 0; o >>= 1) val = ff_add(val, ff_shfl_xor(val, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = val;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kTvThreads / 32; ++w) t += red[w];
-    partial[(size_t)s * gridDim.x + blockIdx.x] = t;
+    FF t = red[0];
+    for (int w = 1; w < kTvThreads / 32; ++w) t = ff_add(t, red[w]);
+    partial[(size_t)s * gridDim.x + blockIdx.x] = ff_to_double(t);
   }
 }
 

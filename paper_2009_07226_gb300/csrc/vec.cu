@@ -2,6 +2,7 @@
 // slice-major natural order and the internal [tile][ordered row][slice]
 // layout, and the CGLS vector updates and FP64 scalars (Eq. 1 with R = 0,
 // CGLS form with one initial back projection, per-slice scalars).
+#include "ff.cuh"
 #include "xct_internal.cuh"
 #include "xct_vec.cuh"
 
@@ -71,30 +72,52 @@ __global__ void __launch_bounds__(kConvThreads) to_natural_kernel(
 // ---------------------------------------------------------------------------
 
 template <int W>
-__device__ void block_slice_sums(const double* part, const uint32_t* pmax, int st, int tile,
+__device__ void block_slice_sums(const FF* part, const uint32_t* pmax, int st, int tile,
                                  double* out_part, uint32_t* out_max, int nbx) {
   // part[W], pmax[W] per thread -> per-slice block totals
-  __shared__ double sd[kVecThreads * 4];
+  __shared__ FF sd[kVecThreads * 4];
   __shared__ uint32_t sm[kVecThreads * 4];
   for (int w = 0; w < W; ++w) {
-    sd[threadIdx.x * W + w] = part ? part[w] : 0.0;
+    sd[threadIdx.x * W + w] = part ? part[w] : FF{0.0f, 0.0f};
     sm[threadIdx.x * W + w] = pmax ? pmax[w] : 0u;
   }
   __syncthreads();
   const int per = st / W;  // threads sharing a slice set repeat every `per`
   for (int sl = threadIdx.x; sl < st; sl += blockDim.x) {
     const int t0 = sl / W, w = sl % W;
-    double acc = 0.0;
+    FF acc{0.0f, 0.0f};
     uint32_t mx = 0;
     for (int t = t0; t < (int)blockDim.x; t += per) {
-      acc += sd[t * W + w];
+      acc = ff_add(acc, sd[t * W + w]);
       mx = max(mx, sm[t * W + w]);
     }
     const int gs = tile * st + sl;
-    if (out_part) out_part[(size_t)gs * nbx + blockIdx.x] = acc;
+    if (out_part) out_part[(size_t)gs * nbx + blockIdx.x] = ff_to_double(acc);
     if (out_max && mx) atomicMax(&out_max[gs], mx);
   }
   __syncthreads();
+}
+
+// W consecutive floats (one 16-byte access for W = 4: element offsets are
+// multiples of 4 and every tile starts on a 16-byte boundary)
+template <int W>
+__device__ __forceinline__ void ldw(const float* p, float (&v)[W]) {
+  if constexpr (W == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+#pragma unroll
+    for (int w = 0; w < W; ++w) v[w] = p[w];
+  }
+}
+template <int W>
+__device__ __forceinline__ void stw(float* p, const float (&v)[W]) {
+  if constexpr (W == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+#pragma unroll
+    for (int w = 0; w < W; ++w) p[w] = v[w];
+  }
 }
 
 // x += alpha p (image); r -= alpha q (sinogram); max |r|, ||r||^2 partials
@@ -113,23 +136,30 @@ __global__ void __launch_bounds__(kVecThreads) update_xr_kernel(
   float* xt = x + (size_t)tile * npix_len;
   const float* pt = p + (size_t)tile * npix_len;
   for (int64_t i = start; i < npix_len; i += stride) {
+    float xv[W], pv[W];
+    ldw<W>(xt + i, xv);
+    ldw<W>(pt + i, pv);
 #pragma unroll
-    for (int w = 0; w < W; ++w) xt[i + w] = fmaf(a[w], pt[i + w], xt[i + w]);
+    for (int w = 0; w < W; ++w) xv[w] = fmaf(a[w], pv[w], xv[w]);
+    stw<W>(xt + i, xv);
   }
   float* rt = r + (size_t)tile * nray_len;
   const float* qt = q + (size_t)tile * nray_len;
-  double ss[W];
+  FF ss[W];
   uint32_t mx[W];
 #pragma unroll
-  for (int w = 0; w < W; ++w) { ss[w] = 0.0; mx[w] = 0u; }
+  for (int w = 0; w < W; ++w) { ss[w] = FF{0.0f, 0.0f}; mx[w] = 0u; }
   for (int64_t i = start; i < nray_len; i += stride) {
+    float rv[W], qv[W];
+    ldw<W>(rt + i, rv);
+    ldw<W>(qt + i, qv);
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      const float v = fmaf(-a[w], qt[i + w], rt[i + w]);
-      rt[i + w] = v;
-      ss[w] += (double)v * (double)v;
-      mx[w] = max(mx[w], __float_as_uint(fabsf(v)));
+      rv[w] = fmaf(-a[w], qv[w], rv[w]);
+      ss[w] = ff_add(ss[w], ff_sq(rv[w]));
+      mx[w] = max(mx[w], __float_as_uint(fabsf(rv[w])));
     }
+    stw<W>(rt + i, rv);
   }
   block_slice_sums<W>(ss, mx, st, tile, rpart, max_r, gridDim.x);
 }
@@ -150,12 +180,15 @@ __global__ void __launch_bounds__(kVecThreads) update_p_kernel(
   float* ptile = p + (size_t)tile * npix_len;
   const float* stile = s + (size_t)tile * npix_len;
   for (int64_t i = start; i < npix_len; i += stride) {
+    float pv[W], sv[W];
+    ldw<W>(ptile + i, pv);
+    ldw<W>(stile + i, sv);
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      const float v = fmaf(bt[w], ptile[i + w], stile[i + w]);
-      ptile[i + w] = v;
-      mx[w] = max(mx[w], __float_as_uint(fabsf(v)));
+      pv[w] = fmaf(bt[w], pv[w], sv[w]);
+      mx[w] = max(mx[w], __float_as_uint(fabsf(pv[w])));
     }
+    stw<W>(ptile + i, pv);
   }
   block_slice_sums<W>(nullptr, mx, st, tile, nullptr, max_p, gridDim.x);
 }
@@ -170,20 +203,24 @@ __global__ void __launch_bounds__(kVecThreads) residual_kernel(
   const int64_t start = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * W;
   float* rt = r + (size_t)tile * nray_len;
   const float* qt = q ? q + (size_t)tile * nray_len : nullptr;
-  double ss[W];
+  FF ss[W];
   uint32_t mx[W];
 #pragma unroll
-  for (int w = 0; w < W; ++w) { ss[w] = 0.0; mx[w] = 0u; }
+  for (int w = 0; w < W; ++w) { ss[w] = FF{0.0f, 0.0f}; mx[w] = 0u; }
   for (int64_t i = start; i < nray_len; i += stride) {
+    float rv[W];
+    ldw<W>(rt + i, rv);
+    if (qt) {
+      float qv[W];
+      ldw<W>(qt + i, qv);
+#pragma unroll
+      for (int w = 0; w < W; ++w) rv[w] = rv[w] - qv[w];
+      stw<W>(rt + i, rv);
+    }
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      float v = rt[i + w];
-      if (qt) {
-        v = v - qt[i + w];
-        rt[i + w] = v;
-      }
-      ss[w] += (double)v * (double)v;
-      mx[w] = max(mx[w], __float_as_uint(fabsf(v)));
+      ss[w] = ff_add(ss[w], ff_sq(rv[w]));
+      mx[w] = max(mx[w], __float_as_uint(fabsf(rv[w])));
     }
   }
   block_slice_sums<W>(ss, mx, st, tile, rpart, max_r, gridDim.x);
@@ -203,18 +240,21 @@ __global__ void __launch_bounds__(kVecThreads) sub_kernel(const float* __restric
   const float* qt = q + (size_t)tile * len;
   const float* yt = y + (size_t)tile * len;
   float* rt = r + (size_t)tile * len;
-  double ss[W];
+  FF ss[W];
   uint32_t mx[W];
 #pragma unroll
-  for (int w = 0; w < W; ++w) { ss[w] = 0.0; mx[w] = 0u; }
+  for (int w = 0; w < W; ++w) { ss[w] = FF{0.0f, 0.0f}; mx[w] = 0u; }
   for (int64_t i = start; i < len; i += stride) {
+    float qv[W], yv[W], rv[W];
+    ldw<W>(qt + i, qv);
+    ldw<W>(yt + i, yv);
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      const float v = qt[i + w] - yt[i + w];
-      rt[i + w] = v;
-      ss[w] += (double)v * (double)v;
-      mx[w] = max(mx[w], __float_as_uint(fabsf(v)));
+      rv[w] = qv[w] - yv[w];
+      ss[w] = ff_add(ss[w], ff_sq(rv[w]));
+      mx[w] = max(mx[w], __float_as_uint(fabsf(rv[w])));
     }
+    stw<W>(rt + i, rv);
   }
   block_slice_sums<W>(ss, mx, st, tile, rpart, max_r, gridDim.x);
 }
