@@ -2,7 +2,9 @@
 // Sec. III-B: input buffering, register reuse, output buffering, multi-stage
 // buffering; Sec. III-C: mixed precision).
 //
-// Two CTAs per SM.  A producer warp takes blocks of 64 rows from a work
+// Two to four CTAs per SM (by the width of a staged row: 128, 64 or 32
+// bytes, i.e. 64 / 32 / 16 slices in 16 bits).  A producer warp takes blocks
+// of 64 rows from a work
 // counter and streams each stage of each block into one of two shared-memory
 // buffers with bulk asynchronous copies (cp.async.bulk) counted in bytes on
 // the buffer's mbarrier: one copy per contiguous run of the stage's staged
@@ -42,6 +44,9 @@ struct PCfg {
   static constexpr int NT = (NC + 1) * 32;         // + one producer warp
   static constexpr bool E16 = XB == 2;
   static constexpr int EB = E16 ? 4 : 8;           // bytes per packed entry
+  // CTAs per SM: narrower staged rows mean fewer consumer warps per CTA
+  // and smaller stage buffers, so more CTAs share an SM
+  static constexpr int MINB = PIXB >= 128 ? 2 : (PIXB == 64 ? 3 : 4);
 };
 
 struct __align__(16) Hdr {
@@ -174,7 +179,7 @@ __device__ __forceinline__ int ceil_log2_exp_p(float m) {
 }
 
 template <class TX, int ST>
-__global__ void __launch_bounds__(PCfg<TX, ST>::NT, kPipeCtasPerSm) spmm_pipe_kernel(PipeArgs a) {
+__global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pipe_kernel(PipeArgs a) {
   using C = PCfg<TX, ST>;
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t bufbytes = a.xbytes + a.ebytes + 256 + 128;
@@ -491,8 +496,10 @@ size_t pipe_smem_bytes(int cap, int64_t emax, int64_t rmax, int pixb, int eb, ui
   return kPipeBufs * (x + e + 256 + 128) + kPipeBufs * list + 128;
 }
 
-// shared memory a pipeline CTA may use so that kPipeCtasPerSm fit on an SM
-constexpr size_t kPipeCtaSmemMax = 113 * 1024;
+// shared memory a pipeline CTA may use so that `minb` CTAs fit on an SM
+// (228 KB per SM, 1 KB of it reserved per CTA)
+constexpr size_t pipe_cta_smem_max(int minb) { return (size_t)(228 * 1024) / minb - 1024; }
+constexpr int pipe_minb(int pixb) { return pixb >= 128 ? 2 : (pixb == 64 ? 3 : 4); }
 
 template <class TX, int ST>
 xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
@@ -541,7 +548,8 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   a.err = list[0].err;
   const size_t smem = pipe_smem_bytes(cap, emax, rmax, C::PIXB, C::EB, &a.xbytes, &a.ebytes,
                                       &a.listbytes);
-  if (smem > kPipeCtaSmemMax) {
+  static_assert(C::MINB == pipe_minb(C::PIXB), "CTAs per SM");
+  if (smem > pipe_cta_smem_max(C::MINB)) {
     set_error("persistent product: %zu bytes of shared memory needed", smem);
     return XCT_ERR_UNSUPPORTED;
   }
@@ -555,7 +563,7 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   XCT_TRY_CUDA(cudaGetDevice(&dev));
   XCT_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (work == 0) return XCT_OK;
-  const int grid = work < sms * kPipeCtasPerSm ? work : sms * kPipeCtasPerSm;
+  const int grid = work < sms * C::MINB ? work : sms * C::MINB;
   XCT_TRY_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int), st));
   spmm_pipe_kernel<TX, ST><<<grid, C::NT, smem, st>>>(a);
   count_launch();
@@ -565,14 +573,21 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
 
 template <class TX>
 xct_status dispatch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
-  // the persistent form is built for 128-byte staged rows only
-  constexpr int kST = 128 / PBytes<TX>::v;
-  for (int i = 0; i < count; ++i)
-    if (list[i].st != kST) {
-      set_error("persistent product: unsupported tile width %d", list[i].st);
-      return XCT_ERR_UNSUPPORTED;
+  // the persistent form is built for staged rows of 32, 64 or 128 bytes
+  // (16, 32 or 64 slices in 16 bits; 8, 16 or 32 in FP32)
+  for (int i = 1; i < count; ++i)
+    if (list[i].st != list[0].st) {
+      set_error("persistent product: products of one launch must share the tile width");
+      return XCT_ERR_INVALID;
     }
-  return launch_pipe<TX, kST>(list, count, st);
+  switch (list[0].st * PBytes<TX>::v) {
+    case 128: return launch_pipe<TX, 128 / PBytes<TX>::v>(list, count, st);
+    case 64: return launch_pipe<TX, 64 / PBytes<TX>::v>(list, count, st);
+    case 32: return launch_pipe<TX, 32 / PBytes<TX>::v>(list, count, st);
+    default:
+      set_error("persistent product: unsupported tile width %d", list[0].st);
+      return XCT_ERR_UNSUPPORTED;
+  }
 }
 
 xct_status pipe_any(const SpmmArgs* list, int count, cudaStream_t s) {
@@ -589,14 +604,15 @@ xct_status pipe_any(const SpmmArgs* list, int count, cudaStream_t s) {
 
 }  // namespace
 
-// The persistent form needs 16-byte lane vectors and 128-byte staged rows
-// (64 slices in 16 bits, 32 in FP32) and two buffers in shared memory.
+// The persistent form needs 16-byte lane vectors, staged rows of 32, 64 or
+// 128 bytes and two buffers in the shared memory of one of its CTAs.
 bool spmm_pipe_applies(const SpmmArgs& a) {
   const int pixb = a.st * (a.storage == XCT_F32 ? 4 : 2);
-  if (pixb != 128 || !a.work || !a.err) return false;
+  if ((pixb != 128 && pixb != 64 && pixb != 32) || !a.work || !a.err) return false;
   if (a.L->nblocks == 0) return false;
-  return pipe_smem_bytes(a.L->cap, a.L->emax_slots, a.L->run_max, 128,
-                         a.storage == XCT_F32 ? 8 : 4, nullptr, nullptr, nullptr) <= kPipeCtaSmemMax;
+  return pipe_smem_bytes(a.L->cap, a.L->emax_slots, a.L->run_max, pixb,
+                         a.storage == XCT_F32 ? 8 : 4, nullptr, nullptr, nullptr) <=
+         pipe_cta_smem_max(pipe_minb(pixb));
 }
 
 xct_status spmm_pipe(const SpmmArgs& a, cudaStream_t s) { return pipe_any(&a, 1, s); }
@@ -606,13 +622,16 @@ bool spmm_pipe_multi_applies(const SpmmArgs* list, int count) {
   int cap = 0;
   int64_t emax = 0, rmax = 0;
   for (int i = 0; i < count; ++i) {
-    if (!spmm_pipe_applies(list[i]) || list[i].storage != list[0].storage) return false;
+    if (!spmm_pipe_applies(list[i]) || list[i].storage != list[0].storage ||
+        list[i].st != list[0].st)
+      return false;
     cap = cap > list[i].L->cap ? cap : list[i].L->cap;
     emax = emax > list[i].L->emax_slots ? emax : list[i].L->emax_slots;
     rmax = rmax > list[i].L->run_max ? rmax : list[i].L->run_max;
   }
-  return pipe_smem_bytes(cap, emax, rmax, 128, list[0].storage == XCT_F32 ? 8 : 4, nullptr, nullptr,
-                         nullptr) <= kPipeCtaSmemMax;
+  const int pixb = list[0].st * (list[0].storage == XCT_F32 ? 4 : 2);
+  return pipe_smem_bytes(cap, emax, rmax, pixb, list[0].storage == XCT_F32 ? 8 : 4, nullptr,
+                         nullptr, nullptr) <= pipe_cta_smem_max(pipe_minb(pixb));
 }
 
 xct_status spmm_pipe_multi(const SpmmArgs* list, int count, cudaStream_t s) {

@@ -118,7 +118,6 @@ inline size_t pipe_buffer_bytes(const Layout& L, int pixb) {
   size_t list = ((size_t)L.run_max * 8 + 127) / 128 * 128;
   return x + e + list + 128 * 2 + 256;
 }
-constexpr int kPipeCtasPerSm = 2;
 #ifndef XCT_PIPE_BUFS
 #define XCT_PIPE_BUFS 2
 #endif
