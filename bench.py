@@ -547,6 +547,68 @@ def run_tv(args):
                       "cost_first": float(lh[0]), "cost_last": float(lh[-1]), "clocks": clocks}))
 
 
+def run_large(args):
+    """The large geometry: 1536^2 grid, 1024 angles, 1536 bins (A with about
+    2.9e9 entries), 32 slices, 30 CGLS iterations, binary16 storage against
+    FP32."""
+    from concurrent.futures import ProcessPoolExecutor
+    from multiprocessing import get_context
+
+    from paper_2009_07226_gb300 import inputs
+    wl = inputs.WORKLOADS["large3d_1536"]
+    S = wl["slices"]
+    with ProcessPoolExecutor(max_workers=os.cpu_count(), mp_context=get_context("spawn")) as ex:
+        parts = list(ex.map(_large_slices, [(s0, min(4, S - s0)) for s0 in range(0, S, 4)]))
+    sino = np.concatenate(parts)
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_07226_gb300 import xct
+    n, m, nd, K = wl["n"], wl["m"], wl["nd"], wl["iters"]
+    stream = torch.cuda.current_stream()
+    y = torch.tensor(sino, dtype=torch.float32, device="cuda")
+    res = {}
+    sampler = ClockSampler(0)
+    sampler.start()
+    xs = {}
+    for kind in ("f16", "f32"):
+        plan = xct.Plan(n, m, nd, kind, cos_sin=inputs.angle_table(m))
+        st = plan.stats()
+        x = torch.empty((S, n, n), device="cuda")
+        for _ in range(args.warmup):
+            xct.xct_cgls(plan.handle, y, x, S, K, xct.XCT_CGLS_TIMING, None, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tp = tb = 0.0
+        e0.record(stream)
+        for _ in range(args.steps):
+            xct.xct_cgls(plan.handle, y, x, S, K, xct.XCT_CGLS_TIMING, None, stream)
+            ps = plan.stats()
+            tp += ps["t_project_ms"] / max(ps["n_project"], 1)
+            tb += ps["t_backproject_ms"] / max(ps["n_backproject"], 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        flops = (2 * K + 1) * 2.0 * st["nnz"] * S
+        res[kind] = {"ms_per_solve": ms, "gflops": flops / (ms * 1e-3) / 1e9,
+                     "project_ms": tp / args.steps, "backproject_ms": tb / args.steps,
+                     "plan_ms": st["plan_ms"], "bytes_a": st["bytes_a"], "bytes_at": st["bytes_at"]}
+        xs[kind] = x
+        plan.close()
+    clocks = sampler.stop()
+    rel = float(torch.linalg.norm(xs["f16"] - xs["f32"]) / torch.linalg.norm(xs["f32"]))
+    print(json.dumps({"mode": "large", "n": n, "angles": m, "bins": nd, "slices": S, "iters": K,
+                      "nnz": st["nnz"], **res, "speedup_mixed_vs_fp32": res["f32"]["ms_per_solve"] /
+                      res["f16"]["ms_per_solve"], "rel_diff_mixed_vs_fp32": rel, "clocks": clocks}))
+
+
+def _large_slices(arg):
+    s0, count = arg
+    from paper_2009_07226_gb300 import inputs
+    return inputs.make_workload("large3d_1536", slices=count, slice_offset=s0, with_images=False)["sino"]
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -554,7 +616,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="cgls", choices=["cgls", "products", "batch", "tv"])
+    ap.add_argument("--mode", default="cgls", choices=["cgls", "products", "batch", "tv", "large"])
     ap.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16"])
     args = ap.parse_args()
     if args.mode == "products":
@@ -563,6 +625,8 @@ def main():
         run_batch(args)
     elif args.mode == "tv":
         run_tv(args)
+    elif args.mode == "large":
+        run_large(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
