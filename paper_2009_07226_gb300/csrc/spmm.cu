@@ -370,11 +370,15 @@ xct_status launch(const SpmmArgs& a, cudaStream_t s) {
   using C = Cfg<TX, ST>;
   const Layout& L = *a.L;
   const size_t smem = C::smem_bytes(L.cap);
-  static int configured_for = -1;  // attribute set per shared-memory size
-  if (configured_for != (int)smem) {
+  // the opt-in shared-memory size is a per-device attribute: set it once per
+  // device and size
+  static std::atomic<int> configured_for[kMaxDevices];
+  int cur_dev = 0;
+  XCT_TRY_CUDA(cudaGetDevice(&cur_dev));
+  if (cur_dev < 0 || cur_dev >= kMaxDevices || configured_for[cur_dev].load() != (int)smem + 1) {
     XCT_TRY_CUDA(cudaFuncSetAttribute(spmm_kernel<TX, ST>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured_for = (int)smem;
+    if (cur_dev >= 0 && cur_dev < kMaxDevices) configured_for[cur_dev].store((int)smem + 1);
   }
   if (L.nblocks == 0 || a.ntiles == 0) return XCT_OK;
   const unsigned char* src = C::E16 ? reinterpret_cast<const unsigned char*>(a.staged16)

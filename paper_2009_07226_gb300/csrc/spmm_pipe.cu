@@ -553,15 +553,18 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
     set_error("persistent product: %zu bytes of shared memory needed", smem);
     return XCT_ERR_UNSUPPORTED;
   }
-  static int configured_for = -1;
-  if (configured_for != (int)smem) {
+  // the opt-in shared-memory size is a per-device attribute: set it once per
+  // device and size
+  static std::atomic<int> configured_for[kMaxDevices];
+  int cur_dev = 0;
+  XCT_TRY_CUDA(cudaGetDevice(&cur_dev));
+  if (cur_dev < 0 || cur_dev >= kMaxDevices || configured_for[cur_dev].load() != (int)smem + 1) {
     XCT_TRY_CUDA(cudaFuncSetAttribute(spmm_pipe_kernel<TX, ST>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured_for = (int)smem;
+    if (cur_dev >= 0 && cur_dev < kMaxDevices) configured_for[cur_dev].store((int)smem + 1);
   }
-  int dev = 0, sms = 0;
-  XCT_TRY_CUDA(cudaGetDevice(&dev));
-  XCT_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int sms = 0;
+  XCT_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur_dev));
   if (work == 0) return XCT_OK;
   const int grid = work < sms * C::MINB ? work : sms * C::MINB;
   XCT_TRY_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int), st));

@@ -19,6 +19,7 @@ namespace xct {
 // ---------------------------------------------------------------------------
 
 void set_error(const char* fmt, ...);
+constexpr int kMaxDevices = 64;   // per-device caches of launch attributes
 extern std::atomic<int64_t> g_launches;
 inline void count_launch(int64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
