@@ -603,6 +603,65 @@ def run_large(args):
                       res["f16"]["ms_per_solve"], "rel_diff_mixed_vs_fp32": rel, "clocks": clocks}))
 
 
+def run_cusparse(args):
+    """Comparison point: cuSPARSE SpMM (through torch.sparse, FP32 CSR times
+    a dense [columns, S] block) on the same A and A^T as the library's FP32
+    and binary16 products, 512^2 x 768 x 512, 64 slices."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_07226_gb300 import inputs, xct
+    wl = inputs.WORKLOADS[WORKLOAD]
+    n, m, nd, S = wl["n"], wl["m"], wl["nd"], wl["slices"]
+    cs = inputs.angle_table(m)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {"mode": "cusparse", "n": n, "angles": m, "bins": nd, "slices": S}
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand((S, n, n), device="cuda", generator=g)
+    y = torch.rand((S, m, nd), device="cuda", generator=g)
+    with xct.Plan(n, m, nd, "f32", cos_sin=cs) as p32:
+        nnz = p32.stats()["nnz"]
+        mats = {}
+        for name, what in (("A", xct.XCT_EXPORT_A_STORED), ("At", xct.XCT_EXPORT_AT_STORED)):
+            rp, col, val = xct.xct_plan_export(p32.handle, what)
+            mats[name] = torch.sparse_csr_tensor(torch.from_numpy(rp), torch.from_numpy(col.astype(np.int64)),
+                                                 torch.from_numpy(val.astype(np.float32)),
+                                                 size=(len(rp) - 1, m * nd if name == "At" else n * n)).cuda()
+        xb = x.reshape(S, -1).t().contiguous()          # [pixels, S]
+        yb = y.reshape(S, -1).t().contiguous()          # [rays, S]
+        out["cusparse_project_ms"] = timed(lambda: torch.sparse.mm(mats["A"], xb), 10)
+        out["cusparse_backproject_ms"] = timed(lambda: torch.sparse.mm(mats["At"], yb), 10)
+        q = torch.sparse.mm(mats["A"], xb).t().reshape(S, m, nd)
+        yo = torch.empty_like(y)
+        out["xct_f32_project_ms"] = timed(lambda: p32.project(x, out=yo), 10)
+        out["max_rel_diff_f32_vs_cusparse"] = float((yo - q).abs().max() / q.abs().max())
+        xo = torch.empty_like(x)
+        out["xct_f32_backproject_ms"] = timed(lambda: p32.backproject(y, out=xo), 10)
+    with xct.Plan(n, m, nd, "f16", cos_sin=cs) as p16:
+        yo = torch.empty_like(y)
+        xo = torch.empty_like(x)
+        out["xct_f16_project_ms"] = timed(lambda: p16.project(x, out=yo), 10)
+        out["xct_f16_backproject_ms"] = timed(lambda: p16.backproject(y, out=xo), 10)
+    for k in ("cusparse_project_ms", "xct_f32_project_ms", "xct_f16_project_ms"):
+        out[k.replace("_ms", "_gflops")] = 2.0 * nnz * S / (out[k] * 1e-3) / 1e9
+    out["note"] = ("library products include the natural <-> internal layout conversions (and the "
+                   "16-bit staging); cuSPARSE is given the dense block already transposed")
+    print(json.dumps(out))
+
+
 def _large_slices(arg):
     s0, count = arg
     from paper_2009_07226_gb300 import inputs
@@ -616,7 +675,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="cgls", choices=["cgls", "products", "batch", "tv", "large"])
+    ap.add_argument("--mode", default="cgls", choices=["cgls", "products", "batch", "tv", "large", "cusparse"])
     ap.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16"])
     args = ap.parse_args()
     if args.mode == "products":
@@ -627,6 +686,8 @@ def main():
         run_tv(args)
     elif args.mode == "large":
         run_large(args)
+    elif args.mode == "cusparse":
+        run_cusparse(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
