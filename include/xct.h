@@ -279,6 +279,29 @@ const char* xct_last_error(void);
 /* Number of kernels this library has launched in the process so far. */
 int64_t xct_launch_count(void);
 
+/*
+ * xct_set_wait_limit -- wall-time limit of every wait inside the persistent
+ * product kernels (a warp waiting for a stage's copies, the producer waiting
+ * for a buffer to be released, the block-end rendezvous).  Default 2 s.  A
+ * wait that runs out sets the plan's error flag; the kernel lets the copies
+ * it already issued land (with its own 2 s limit) and returns, so the GPU
+ * context stays usable.  0 makes every wait that is not already satisfied
+ * give up at once (a way to exercise this path).  previous: NULL or the
+ * limit before the call.  XCT_ERR_INVALID above 60 s.  Process-wide; read
+ * at each launch.  The paper has no counterpart.
+ */
+xct_status xct_set_wait_limit(uint64_t ns, uint64_t* previous);
+
+/*
+ * xct_plan_check -- synchronise `stream` and report whether a wait inside a
+ * product kernel of this plan ran out since the last check (XCT_ERR_TIMEOUT;
+ * the flag is cleared).  Calls that return results to the host, and
+ * xct_cgls, xct_cgls_batch and xct_tv_reconstruct, check the flag
+ * themselves; products into device buffers are asynchronous and are checked
+ * here.
+ */
+xct_status xct_plan_check(xct_plan_t plan, void* stream);
+
 /* Library version string. */
 const char* xct_version(void);
 

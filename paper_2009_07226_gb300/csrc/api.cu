@@ -19,6 +19,8 @@ namespace xct {
 
 static thread_local char g_err[1024] = "";
 std::atomic<int64_t> g_launches{0};
+std::atomic<uint64_t> g_wait_ns{2000000000ull};
+uint64_t wait_limit_ns() { return g_wait_ns.load(std::memory_order_relaxed); }
 
 void set_error(const char* fmt, ...) {
   va_list ap;
@@ -547,6 +549,35 @@ xct_status xct_set_allocator(xct_alloc_fn alloc, xct_free_fn release, void* ctx)
 const char* xct_last_error(void) { return g_err; }
 
 int64_t xct_launch_count(void) { return g_launches.load(); }
+
+xct_status xct_set_wait_limit(uint64_t ns, uint64_t* previous) {
+  if (ns > 60000000000ull) {
+    set_error("wait limit %llu ns above 60 s", (unsigned long long)ns);
+    return XCT_ERR_INVALID;
+  }
+  const uint64_t old = g_wait_ns.exchange(ns);
+  if (previous) *previous = old;
+  return XCT_OK;
+}
+
+xct_status xct_plan_check(xct_plan_t plan, void* stream) {
+  if (!plan) {
+    set_error("plan is NULL");
+    return XCT_ERR_INVALID;
+  }
+  Plan& p = *static_cast<Plan*>(plan);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int e = 0;
+  XCT_TRY_CUDA(cudaMemcpyAsync(&e, p.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  if (e) {
+    XCT_TRY_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), s));
+    XCT_TRY_CUDA(cudaStreamSynchronize(s));
+    set_error("a bounded wait in a product kernel of this plan ran out; its results are invalid");
+    return XCT_ERR_TIMEOUT;
+  }
+  return XCT_OK;
+}
 
 const char* xct_version(void) { return "xct 0.1.0 (sm_103a)"; }
 

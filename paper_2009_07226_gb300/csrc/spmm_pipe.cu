@@ -85,6 +85,7 @@ struct PipeArgs {
   int* work;
   int* err;
   uint32_t xbytes, ebytes;   // per-buffer region sizes (128-byte multiples)
+  uint64_t wait_ns;          // limit of every pipeline wait
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -114,20 +115,37 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// non-blocking test of the phase of `parity`
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(su32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ uint64_t now_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for the phase of `parity` to complete; false after ~2 s.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Wait for the phase of `parity` to complete; false once `limit_ns` of wall
+// time has passed without it (checked every 256 tries; a limit of 0 only
+// tests the phase once, without suspending).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (limit_ns == 0) return mbar_test(bar, parity);   // no waiting at all
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = now_ns();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try(bar, parity)) return true;
-    if ((i & 255u) == 0 && now_ns() - t0 > 2000000000ull) return false;
+    if ((i & 255u) == 0 && now_ns() - t0 > limit_ns) return false;
   }
 }
+// the limit of the waits that let copies already issued land before a CTA
+// that gave up exits (independent of the configurable limit)
+constexpr uint64_t kDrainNs = 2000000000ull;
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -189,6 +207,7 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pip
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + NB * bufbytes + NB * listbytes);
   uint64_t* empty = full + NB;
   uint64_t* plbar = full + 2 * NB;   // run list of a stage landed
+  uint64_t* redbar = full + 3 * NB;  // consumers' rendezvous at a block end (2)
   auto plist = [&](int slot) { return lists + (size_t)slot * (listbytes / 8); };
   auto xbuf = [&](int b) { return smem + b * bufbytes; };
   auto ebuf = [&](int b) { return smem + b * bufbytes + a.xbytes; };
@@ -202,6 +221,8 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pip
       mbar_init(&empty[b], C::NC);
       mbar_init(&plbar[b], 1);
     }
+    mbar_init(&redbar[0], C::NC);
+    mbar_init(&redbar[1], C::NC);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // zero slot of each product (row `cap` of its layout) in every buffer:
@@ -266,7 +287,7 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pip
       }
     };
     bool ok = true;
-    uint32_t fail_it = 0;
+    uint32_t fail_it = 0, req_hi = 0;   // req_hi: last stage whose run list was requested
     Ref cur = fetch();
     request(cur, 0);
     for (uint32_t it = 0;; ++it) {
@@ -284,11 +305,12 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pip
         // the copy into it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         request(nxt, buf + 1 == NB ? 0 : buf + 1);
+        req_hi = it + 1;
       }
-      if (!mbar_wait(&empty[buf], (use & 1) ^ 1)) { ok = false; fail_it = it; break; }
+      if (!mbar_wait(&empty[buf], (use & 1) ^ 1, a.wait_ns)) { ok = false; fail_it = it; break; }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       const bool real = cur.w >= 0 && cur.s >= 0;
-      if (real && !mbar_wait(&plbar[buf], use & 1)) { ok = false; fail_it = it; break; }
+      if (real && !mbar_wait(&plbar[buf], use & 1, a.wait_ns)) { ok = false; fail_it = it; break; }
       const PipeLayout& P = a.L[cur.l];
       const int tile = cur.w >= 0 ? cur.wl / P.nblocks : 0;
       const unsigned char* xt = P.xs + (size_t)tile * P.ncols * C::PIXB;
@@ -334,11 +356,13 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pip
     if (!ok) {
       if (lane == 0) atomicExch(a.err, 1);
       // let copies already issued land before the CTA's shared memory goes
-      // away: the last NB iterations before the failing one completed their
-      // arrivals on the full barriers (every iteration arrives, with copies
-      // or without)
+      // away: the stage copies of the last NB iterations before the failing
+      // one (every iteration arrives on its full barrier, with copies or
+      // without), and the run lists requested for stages fail_it and
+      // fail_it + 1 (every request completes a phase of its list barrier)
       for (uint32_t j = fail_it > (uint32_t)NB ? fail_it - NB : 0; j < fail_it; ++j)
-        mbar_wait(&full[j % NB], (j / NB) & 1);
+        mbar_wait(&full[j % NB], (j / NB) & 1, kDrainNs);
+      for (uint32_t j = fail_it; j <= req_hi; ++j) mbar_wait(&plbar[j % NB], (j / NB) & 1, kDrainNs);
     }
     return;
   }
@@ -350,9 +374,10 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pip
   float acc[C::SPL];
 #pragma unroll
   for (int i = 0; i < C::SPL; ++i) acc[i] = 0.0f;
+  uint32_t rphase = 0;   // phase of the block-end rendezvous barriers
   for (uint32_t it = 0;; ++it) {
     const int buf = (int)(it % kPipeBufs);
-    if (!mbar_wait(&full[buf], (it / kPipeBufs) & 1)) {
+    if (!mbar_wait(&full[buf], (it / kPipeBufs) & 1, a.wait_ns)) {
       if (lane == 0) atomicExch(a.err, 1);
       return;
     }
@@ -459,7 +484,14 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pip
         // consumer warp is here: their area holds the [NC][ST] partials
         // (the buffer is released only after the reduction)
         double* red = reinterpret_cast<double*>(xbuf(buf));
-        asm volatile("bar.sync 1, %0;" ::"r"(C::NC * 32) : "memory");   // consumers only
+        // consumers only, bounded: a warp that gave up earlier cannot leave
+        // the others waiting
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&redbar[0]);
+        if (!mbar_wait(&redbar[0], rphase, a.wait_ns)) {
+          if (lane == 0) atomicExch(a.err, 1);
+          return;
+        }
         if (rw == 0) {
 #pragma unroll
           for (int v = 0; v < C::VPL; ++v)
@@ -467,7 +499,13 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pip
             for (int e = 0; e < C::EPV; ++e)
               red[warp * ST + v * C::LPR * C::EPV + sub * C::EPV + e] = d[v * C::EPV + e];
         }
-        asm volatile("bar.sync 1, %0;" ::"r"(C::NC * 32) : "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&redbar[1]);
+        if (!mbar_wait(&redbar[1], rphase, a.wait_ns)) {
+          if (lane == 0) atomicExch(a.err, 1);
+          return;
+        }
+        rphase ^= 1u;
         if (warp == 0) {
           for (int sl = lane; sl < ST; sl += 32) {
             double t = 0.0;
@@ -546,6 +584,7 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   a.cap = cap;
   a.work = list[0].work;
   a.err = list[0].err;
+  a.wait_ns = wait_limit_ns();
   const size_t smem = pipe_smem_bytes(cap, emax, rmax, C::PIXB, C::EB, &a.xbytes, &a.ebytes,
                                       &a.listbytes);
   static_assert(C::MINB == pipe_minb(C::PIXB), "CTAs per SM");

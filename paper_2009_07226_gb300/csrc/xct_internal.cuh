@@ -19,6 +19,8 @@ namespace xct {
 // ---------------------------------------------------------------------------
 
 void set_error(const char* fmt, ...);
+// limit of the bounded waits inside the persistent kernels (xct_set_wait_limit)
+uint64_t wait_limit_ns();
 constexpr int kMaxDevices = 64;   // per-device caches of launch attributes
 extern std::atomic<int64_t> g_launches;
 inline void count_launch(int64_t k = 1) { g_launches.fetch_add(k, std::memory_order_relaxed); }

@@ -96,6 +96,8 @@ _SIGNATURES = [
     ("xct_set_allocator", ctypes.c_int, [ALLOC_FN, FREE_FN, ctypes.c_void_p]),
     ("xct_last_error", ctypes.c_char_p, []),
     ("xct_launch_count", ctypes.c_int64, []),
+    ("xct_set_wait_limit", ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+    ("xct_plan_check", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("xct_version", ctypes.c_char_p, []),
 ]
 
@@ -285,6 +287,20 @@ def xct_last_error() -> str:
 
 def xct_launch_count() -> int:
     return lib().xct_launch_count()
+
+
+def xct_set_wait_limit(ns: int) -> int:
+    """Set the limit of the waits inside the persistent kernels; returns the
+    previous limit (nanoseconds)."""
+    prev = ctypes.c_uint64()
+    _check(lib().xct_set_wait_limit(ns, ctypes.byref(prev)))
+    return prev.value
+
+
+def xct_plan_check(plan: int, stream=None) -> None:
+    """Raise XctError(XCT_ERR_TIMEOUT) if a product of this plan gave up a
+    wait since the last check."""
+    _check(lib().xct_plan_check(plan, _stream(stream)))
 
 
 def xct_version() -> str:
