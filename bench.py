@@ -219,7 +219,7 @@ def run_ours(args):
     n, m, nd, S, K = w["n"], w["m"], w["nd"], w["slices"], w["iters"]
     y = torch.tensor(w["sino"], dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    plans = {k: xct.Plan(n, m, nd, k, cos_sin=w["cos_sin"]) for k in ("f16", "f32")}
+    plans = {k: xct.Plan(n, m, nd, k, cos_sin=w["cos_sin"]) for k in ("f16", "f32", "f16a")}
     nnz = plans["f16"].stats()["nnz"]
     flops_step = (2 * K + 1) * 2.0 * nnz * S
     xs = {k: torch.empty((S, n, n), dtype=torch.float32, device=dev) for k in plans}
@@ -254,7 +254,7 @@ def run_ours(args):
         ms = shard.max_over_ranks(ev0.elapsed_time(ev1) / steps, dev)
         return ms, tp / max(npj, 1), tb / max(nbp, 1), to / steps, launches
 
-    for kind in ("f16", "f32"):
+    for kind in ("f16", "f32", "f16a"):
         for _ in range(args.warmup):
             step(kind)
     torch.cuda.synchronize()
@@ -265,6 +265,7 @@ def run_ours(args):
         sampler.start()
     ms16, proj16, back16, other16, launches = timed("f16", args.steps)
     ms32, proj32, back32, other32, _ = timed("f32", args.steps)
+    msa, proja, backa, othera, _ = timed("f16a", args.steps)
     clocks = sampler.stop() if sampler else None
 
     # graph path (the default call) for reference, untimed by the roofline
@@ -296,6 +297,8 @@ def run_ours(args):
         xct.xct_cgls(plans[kind].handle, y, xs[kind], S, K, 0, lg, stream)
         logs[kind] = lg[:, :, 0]
     track = (logs["f16"] / logs["f32"] - 1.0).abs()
+    track_a = (logs["f16a"] / logs["f32"] - 1.0).abs()
+    rel_a = float(torch.linalg.norm(xs["f16a"] - xs["f32"]) / torch.linalg.norm(xs["f32"]))
     q16, q32 = plans["f16"].project(xs["f32"]), plans["f32"].project(xs["f32"])
     proj_err = float(torch.linalg.norm((q16 - q32).double()) / torch.linalg.norm(q32.double()))
     track_max, track_final = float(track.max()), float(track[-1].max())
@@ -342,6 +345,13 @@ def run_ours(args):
         "hbm_gbs_alg": (alg_bytes * K + alg_bytes_bp * (K + 1)) / (ms16 * 1e-3) / 1e9,
         "rel_err_mixed_vs_fp32": rel,
         "residual_curve_mixed_vs_fp32": {"max_rel_dev": track_max, "final_rel_dev": track_final},
+        "mixed_fp32_vectors": {"storage": "f16a (binary16 matrix, FP32 slices)",
+                               "value": flops_step / (msa * 1e-3) / 1e9, "unit": "GFLOP/s",
+                               "ms_per_step": msa, "speedup_vs_fp32": ms32 / msa,
+                               "project_ms": proja, "backproject_ms": backa,
+                               "residual_curve_vs_fp32": {"max_rel_dev": float(track_a.max()),
+                                                          "final_rel_dev": float(track_a[-1].max())},
+                               "rel_err_vs_fp32": rel_a},
         "rel_err_projection_mixed_vs_fp32": proj_err,
         "graph_ms_per_step": graph_ms,
         "kernel_ms": {"project_f16": proj16, "backproject_f16": back16, "other_f16_per_step": other16,

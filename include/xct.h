@@ -55,8 +55,17 @@ typedef enum {
  * vectors in float32.  XCT_F16 / XCT_BF16: matrix values stored as
  * RN16(l * 2^k) (k = 15 for binary16, 0 for bfloat16), input vectors
  * normalised per slice by 2^-ceil(log2 max|v_s|) and staged in 16 bits,
- * products accumulated in float32, outputs float32. */
-typedef enum { XCT_F32 = 0, XCT_F16 = 1, XCT_BF16 = 2 } xct_dtype;
+ * products accumulated in float32, outputs float32.  XCT_F16A / XCT_BF16A:
+ * the same 16-bit matrix values with the input vectors staged in float32
+ * (no normalisation): the matrix bytes of the 16-bit forms, the vector
+ * rounding of the float32 form. */
+typedef enum {
+  XCT_F32 = 0,
+  XCT_F16 = 1,
+  XCT_BF16 = 2,
+  XCT_F16A = 3,
+  XCT_BF16A = 4
+} xct_dtype;
 
 typedef struct {
   int32_t n;              /* grid side (pixels), 1 <= n <= 32768 */

@@ -438,6 +438,18 @@ def mixed_project(a: CSR, X: np.ndarray, kind: str) -> np.ndarray:
     return Y * (2.0 ** (e.astype(np.float64) - k))[:, None]
 
 
+def matrix16_project(a: CSR, X: np.ndarray, kind: str) -> np.ndarray:
+    """The product with only the matrix in 16 bits (the storage half of Sec.
+    III-C): entries RN16(l * 2**k), input slices kept in single precision,
+    products summed (here exactly, in FP64) and multiplied by 2**-k.  kind
+    'f16' or 'bf16' names the value format."""
+    rnd = _ROUND[kind]
+    k = MATRIX_SCALE_EXP[kind]
+    X32 = np.asarray(X, dtype=np.float32).reshape(-1, a.ncol).astype(np.float64)
+    aq = CSR(a.nrow, a.ncol, a.rowptr, a.col, rnd(a.val * 2.0 ** k))
+    return csr_mm(aq, X32) * 2.0 ** -k
+
+
 # --------------------------------------------------------------------------
 # Smoothed total variation (a reading of R(x) in Eq. 1)
 # --------------------------------------------------------------------------

@@ -245,7 +245,7 @@ xct_status cgls_impl(Plan& p, const float* y, float* x, int32_t S, int32_t iters
   XCT_TRY(ar.get(&B.Sv, (size_t)p.npix * S_pad));
   XCT_TRY(ar.get(&B.R, (size_t)p.nray * S_pad));
   XCT_TRY(ar.get(&B.Q, (size_t)p.nray * S_pad));
-  if (p.storage != XCT_F32) {
+  if (stages16(p.storage)) {
     XCT_TRY(ar.get(&B.h_pix, (size_t)p.npix * S_pad));
     XCT_TRY(ar.get(&B.h_ray, (size_t)p.nray * S_pad));
   }
@@ -356,7 +356,7 @@ xct_status apply_impl(Plan& p, bool transposed, const float* in, float* out, int
   XCT_TRY(ar.get(&Yi, (size_t)nout * S_pad));
   XCT_TRY(ar.get(&mx, (size_t)S_pad));
   uint16_t* h16 = nullptr;
-  if (p.storage != XCT_F32) XCT_TRY(ar.get(&h16, (size_t)nin * S_pad));
+  if (stages16(p.storage)) XCT_TRY(ar.get(&h16, (size_t)nin * S_pad));
   int* work;
   XCT_TRY(ar.get(&work, 1));
   XCT_TRY_CUDA(cudaMemsetAsync(mx, 0, sizeof(uint32_t) * S_pad, s));
@@ -416,8 +416,8 @@ xct_status xct_plan(const xct_geometry* g, xct_dtype storage, uint32_t flags, vo
     set_error("det_spacing must be finite and nonzero, det_offset finite, min_seg finite >= 0");
     return XCT_ERR_INVALID;
   }
-  if (storage != XCT_F32 && storage != XCT_F16 && storage != XCT_BF16) {
-    set_error("storage %d is not XCT_F32, XCT_F16 or XCT_BF16", (int)storage);
+  if (!valid_storage(storage)) {
+    set_error("storage %d is not XCT_F32, XCT_F16, XCT_BF16, XCT_F16A or XCT_BF16A", (int)storage);
     return XCT_ERR_INVALID;
   }
   if (flags & ~XCT_PLAN_KEEP_F64) {

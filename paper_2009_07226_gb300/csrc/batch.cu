@@ -64,8 +64,8 @@ xct_status choose_tile(Plan& p, int S, bool tune, cudaStream_t s, int* out) {
     *out = it->second;
     return XCT_OK;
   }
-  const std::vector<int> cand = p.storage == XCT_F32 ? std::vector<int>{8, 16, 32}
-                                                     : std::vector<int>{16, 32, 64};
+  const std::vector<int> cand = stages16(p.storage) ? std::vector<int>{16, 32, 64}
+                                                     : std::vector<int>{8, 16, 32};
   double best = 1e300;
   int best_st = pick_slices_per_tile(p.storage, S);
   for (int st : cand) {
@@ -78,7 +78,7 @@ xct_status choose_tile(Plan& p, int S, bool tune, cudaStream_t s, int* out) {
     int* work;
     XCT_TRY(ar.get(&xi, (size_t)p.npix * S_pad));
     XCT_TRY(ar.get(&yi, (size_t)p.nray * S_pad));
-    if (p.storage != XCT_F32) XCT_TRY(ar.get(&h, (size_t)std::max(p.npix, p.nray) * S_pad));
+    if (stages16(p.storage)) XCT_TRY(ar.get(&h, (size_t)std::max(p.npix, p.nray) * S_pad));
     XCT_TRY(ar.get(&mx, (size_t)S_pad));
     XCT_TRY(ar.get(&work, 1));
     XCT_TRY_CUDA(cudaMemsetAsync(xi, 0, sizeof(float) * p.npix * S_pad, s));
@@ -127,7 +127,7 @@ xct_status alloc_group(Group& g, int iters, Arena& ar) {
   XCT_TRY(ar.get(&g.Sv, np));
   XCT_TRY(ar.get(&g.R, nr));
   XCT_TRY(ar.get(&g.Q, nr));
-  if (p.storage != XCT_F32) {
+  if (stages16(p.storage)) {
     XCT_TRY(ar.get(&g.h_pix, np));
     XCT_TRY(ar.get(&g.h_ray, nr));
   }

@@ -93,7 +93,7 @@ extern "C" xct_status xct_project_noalloc(xct_plan_t plan, const float* x, float
   // copy, per-slice maxima, work counter
   const size_t b_xi = align256(sizeof(float) * (size_t)L.ncols * S_pad);
   const size_t b_yi = align256(sizeof(float) * (size_t)L.nrows * S_pad);
-  const size_t b_h = p.storage != XCT_F32 ? align256(sizeof(uint16_t) * (size_t)L.ncols * S_pad) : 0;
+  const size_t b_h = stages16(p.storage) ? align256(sizeof(uint16_t) * (size_t)L.ncols * S_pad) : 0;
   const size_t b_mx = align256(sizeof(uint32_t) * S_pad);
   const size_t b_w = 256;
   const size_t need = b_xi + b_yi + b_h + b_mx + b_w;

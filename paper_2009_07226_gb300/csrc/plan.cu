@@ -868,7 +868,7 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
   if (nb > 0) {
     if (storage == XCT_F32)
       fill_entries_kernel<0><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent);
-    else if (storage == XCT_F16)
+    else if (half_values(storage))
       fill_entries_kernel<1><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent);
     else
       fill_entries_kernel<2><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent);
@@ -893,7 +893,7 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
   const xct_geometry& g = p.g;
   p.npix = (int64_t)g.n * g.n;
   p.nray = (int64_t)g.n_angles * g.n_det;
-  p.mat_scale_exp = p.storage == XCT_F16 ? 15 : 0;
+  p.mat_scale_exp = half_values(p.storage) ? 15 : 0;
   const int T = g.hilbert_tile > 0 ? g.hilbert_tile : 8;
   Arena& keep = p.mem;
   keep.stream = s;
@@ -1081,7 +1081,7 @@ xct_status export_matrix(Plan& p, int what, int64_t* rowptr, int32_t* col, doubl
                 uint32_t w = e4[slot];
                 idx = w & 0xffffu;
                 uint16_t h = (uint16_t)(w >> 16);
-                if (p.storage == XCT_F16) {
+                if (half_values(p.storage)) {
                   __half_raw hr;
                   hr.x = h;
                   v = (double)__half2float(__half(hr));

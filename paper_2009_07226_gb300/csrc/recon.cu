@@ -66,7 +66,7 @@ extern "C" xct_status xct_tv_reconstruct(xct_plan_t plan, const float* y, float*
   XCT_TRY(ar.get(&Q, (size_t)S_pad * nray));
   XCT_TRY(ar.get(&R, (size_t)S_pad * nray));
   XCT_TRY(ar.get(&Yi, (size_t)S_pad * nray));
-  if (p.storage != XCT_F32) {
+  if (stages16(p.storage)) {
     XCT_TRY(ar.get(&h_pix, (size_t)S_pad * npix));
     XCT_TRY(ar.get(&h_ray, (size_t)S_pad * nray));
   }

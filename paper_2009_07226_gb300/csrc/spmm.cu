@@ -441,14 +441,16 @@ bool spmm_supported(xct_dtype storage, int st) {
 }
 
 int pick_slices_per_tile(xct_dtype storage, int S) {
-  const int maxst = storage == XCT_F32 ? 32 : 64;
-  int st = 1;
+  // 128-byte staged rows at most; FP32 staged rows of 16-bit matrices at
+  // least 32 bytes (the persistent kernel is their only form)
+  const int maxst = stages16(storage) ? 64 : 32;
+  int st = matrix16(storage) && !stages16(storage) ? 8 : 1;
   while (st < S && st < maxst) st <<= 1;
   return st;
 }
 
 xct_status spmm_stage(const SpmmArgs& a, cudaStream_t s) {
-  if (a.storage == XCT_F32) return XCT_OK;
+  if (!stages16(a.storage)) return XCT_OK;
   if (!a.staged16) {
     set_error("16-bit storage needs a staging buffer");
     return XCT_ERR_INVALID;
@@ -462,11 +464,16 @@ xct_status spmm_run(const SpmmArgs& a, cudaStream_t s) {
     set_error("stage capacity %d exceeds the 16-bit index", a.L->cap);
     return XCT_ERR_UNSUPPORTED;
   }
-  if (a.storage != XCT_F32 && a.storage != XCT_F16 && a.storage != XCT_BF16) {
+  if (!valid_storage(a.storage)) {
     set_error("unknown storage type");
     return XCT_ERR_INVALID;
   }
   if (spmm_pipe_applies(a)) return spmm_pipe(a, s);
+  if (matrix16(a.storage) && !stages16(a.storage)) {
+    set_error("16-bit matrix with FP32 vectors needs the persistent product (tile width %d, "
+              "stage capacity %d)", a.st, a.L->cap);
+    return XCT_ERR_UNSUPPORTED;
+  }
   switch (a.storage) {
     case XCT_F32: return dispatch<float>(a, s);
     case XCT_F16: return dispatch<__half>(a, s);

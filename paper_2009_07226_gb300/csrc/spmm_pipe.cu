@@ -30,7 +30,8 @@ template <> struct PBytes<float> { static constexpr int v = 4; };
 template <> struct PBytes<__half> { static constexpr int v = 2; };
 template <> struct PBytes<__nv_bfloat16> { static constexpr int v = 2; };
 
-template <class TX, int ST>
+// TX: type of the staged input rows; TW: type of the stored matrix values
+template <class TX, class TW, int ST>
 struct PCfg {
   static constexpr int XB = PBytes<TX>::v;
   static constexpr int PIXB = ST * XB;
@@ -42,8 +43,9 @@ struct PCfg {
   static constexpr int RPW = 32 / LPR;
   static constexpr int NC = kRowsPerBlock / RPW;   // consumer warps
   static constexpr int NT = (NC + 1) * 32;         // + one producer warp
-  static constexpr bool E16 = XB == 2;
-  static constexpr int EB = E16 ? 4 : 8;           // bytes per packed entry
+  static constexpr bool X16 = XB == 2;             // normalised 16-bit staged rows
+  static constexpr bool W16 = PBytes<TW>::v == 2;  // {u16 index, 16-bit value} entries
+  static constexpr int EB = W16 ? 4 : 8;           // bytes per packed entry
   // CTAs per SM: narrower staged rows mean fewer consumer warps per CTA
   // and smaller stage buffers, so more CTAs share an SM
   static constexpr int MINB = PIXB >= 128 ? 2 : (PIXB == 64 ? 3 : 4);
@@ -155,8 +157,8 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 
 // mixed-precision FMA of one staged 16-byte vector (see spmm.cu)
-template <class TX, int EPV> struct PFma;
-template <int EPV> struct PFma<float, EPV> {
+template <class TX, class TW, int EPV> struct PFma;
+template <int EPV> struct PFma<float, float, EPV> {
   static __device__ __forceinline__ void run(float* acc, const uint4& v, uint32_t wbits) {
     const float w = __uint_as_float(wbits);
     const float* x = reinterpret_cast<const float*>(&v);
@@ -164,7 +166,7 @@ template <int EPV> struct PFma<float, EPV> {
     for (int e = 0; e < EPV; ++e) acc[e] = fmaf(w, x[e], acc[e]);
   }
 };
-template <int EPV> struct PFma<__half, EPV> {
+template <int EPV> struct PFma<__half, __half, EPV> {
   static __device__ __forceinline__ void run(float* acc, const uint4& v, uint32_t wbits) {
     const unsigned short w = (unsigned short)wbits;
     const uint32_t* x = reinterpret_cast<const uint32_t*>(&v);
@@ -176,7 +178,7 @@ template <int EPV> struct PFma<__half, EPV> {
           : "r"(x[e]), "h"(w));
   }
 };
-template <int EPV> struct PFma<__nv_bfloat16, EPV> {
+template <int EPV> struct PFma<__nv_bfloat16, __nv_bfloat16, EPV> {
   static __device__ __forceinline__ void run(float* acc, const uint4& v, uint32_t wbits) {
     const unsigned short w = (unsigned short)wbits;
     const uint32_t* x = reinterpret_cast<const uint32_t*>(&v);
@@ -189,6 +191,25 @@ template <int EPV> struct PFma<__nv_bfloat16, EPV> {
   }
 };
 
+// FP32 staged rows times a 16-bit matrix value: the value converted once
+// (exactly), then FP32 FMAs
+template <int EPV> struct PFma<float, __half, EPV> {
+  static __device__ __forceinline__ void run(float* acc, const uint4& v, uint32_t wbits) {
+    const float w = __half2float(__ushort_as_half((unsigned short)wbits));
+    const float* x = reinterpret_cast<const float*>(&v);
+#pragma unroll
+    for (int e = 0; e < EPV; ++e) acc[e] = fmaf(w, x[e], acc[e]);
+  }
+};
+template <int EPV> struct PFma<float, __nv_bfloat16, EPV> {
+  static __device__ __forceinline__ void run(float* acc, const uint4& v, uint32_t wbits) {
+    const float w = __uint_as_float((wbits & 0xffffu) << 16);
+    const float* x = reinterpret_cast<const float*>(&v);
+#pragma unroll
+    for (int e = 0; e < EPV; ++e) acc[e] = fmaf(w, x[e], acc[e]);
+  }
+};
+
 __device__ __forceinline__ int ceil_log2_exp_p(float m) {
   if (!(m > 0.0f)) return 0;
   int ex;
@@ -196,9 +217,10 @@ __device__ __forceinline__ int ceil_log2_exp_p(float m) {
   return f == 0.5f ? ex - 1 : ex;
 }
 
-template <class TX, int ST>
-__global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pipe_kernel(PipeArgs a) {
-  using C = PCfg<TX, ST>;
+template <class TX, class TW, int ST>
+__global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
+    spmm_pipe_kernel(PipeArgs a) {
+  using C = PCfg<TX, TW, ST>;
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t bufbytes = a.xbytes + a.ebytes + 256 + 128;
   const uint32_t listbytes = a.listbytes;
@@ -396,7 +418,7 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pip
       const int cnt = (int)((cw >> ((gq & 1) * 16)) & 0xffffu);
       const int nch = (cnt + 3) >> 2;
       const unsigned char* xs = xbuf(buf) + sub * C::VB;
-      if constexpr (C::E16) {
+      if constexpr (C::W16) {
         const uint4* ep = reinterpret_cast<const uint4*>(ebuf(buf) + (off - base) * 4) + gq;
         uint4 nx = nch > 0 ? ep[0] : make_uint4(0, 0, 0, 0);
         for (int c = 0; c < nch; ++c) {
@@ -413,7 +435,8 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pip
 #pragma unroll
           for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int v = 0; v < C::VPL; ++v) PFma<TX, C::EPV>::run(acc + v * C::EPV, xv[q][v], e4[q] >> 16);
+            for (int v = 0; v < C::VPL; ++v)
+              PFma<TX, TW, C::EPV>::run(acc + v * C::EPV, xv[q][v], e4[q] >> 16);
         }
       } else {
         const uint4* ep = reinterpret_cast<const uint4*>(ebuf(buf) + (off - base) * 8) + gq * 2;
@@ -433,7 +456,7 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pip
 #pragma unroll
           for (int q = 0; q < 4; ++q)
 #pragma unroll
-            for (int v = 0; v < C::VPL; ++v) PFma<TX, C::EPV>::run(acc + v * C::EPV, xv[q][v], val[q]);
+            for (int v = 0; v < C::VPL; ++v) PFma<TX, TW, C::EPV>::run(acc + v * C::EPV, xv[q][v], val[q]);
         }
       }
     }
@@ -453,9 +476,11 @@ __global__ void __launch_bounds__(PCfg<TX, ST>::NT, PCfg<TX, ST>::MINB) spmm_pip
         for (int e = 0; e < C::EPV; ++e) {
           const int sl = v * C::LPR * C::EPV + sub * C::EPV + e;
           float scale = 1.0f;
-          if (C::E16)
+          if constexpr (C::X16)
             scale = ldexpf(1.0f, ceil_log2_exp_p(__uint_as_float(__ldg(P.in_max + tile * ST + sl))) -
                                      P.mat_scale_exp);
+          else if constexpr (C::W16)
+            scale = ldexpf(1.0f, -P.mat_scale_exp);
           r[v * C::EPV + e] = acc[v * C::EPV + e] * scale;
         }
       if (row < P.nrows) {
@@ -539,9 +564,9 @@ size_t pipe_smem_bytes(int cap, int64_t emax, int64_t rmax, int pixb, int eb, ui
 constexpr size_t pipe_cta_smem_max(int minb) { return (size_t)(228 * 1024) / minb - 1024; }
 constexpr int pipe_minb(int pixb) { return pixb >= 128 ? 2 : (pixb == 64 ? 3 : 4); }
 
-template <class TX, int ST>
+template <class TX, class TW, int ST>
 xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
-  using C = PCfg<TX, ST>;
+  using C = PCfg<TX, TW, ST>;
   // the block-end reduction reuses a buffer's staged-row area
   static_assert((size_t)C::NC * ST * sizeof(double) <= (size_t)65 * C::PIXB,
                 "reduction area must fit in the staged rows of the smallest stage buffer");
@@ -568,7 +593,7 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
     P.nblocks = L.nblocks;
     P.ntiles = s.ntiles;
     P.work_begin = work;
-    P.xs = C::E16 ? reinterpret_cast<const unsigned char*>(s.staged16)
+    P.xs = C::X16 ? reinterpret_cast<const unsigned char*>(s.staged16)
                   : reinterpret_cast<const unsigned char*>(s.x);
     P.y = s.y;
     P.in_max = s.in_max;
@@ -598,7 +623,7 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   int cur_dev = 0;
   XCT_TRY_CUDA(cudaGetDevice(&cur_dev));
   if (cur_dev < 0 || cur_dev >= kMaxDevices || configured_for[cur_dev].load() != (int)smem + 1) {
-    XCT_TRY_CUDA(cudaFuncSetAttribute(spmm_pipe_kernel<TX, ST>,
+    XCT_TRY_CUDA(cudaFuncSetAttribute(spmm_pipe_kernel<TX, TW, ST>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (cur_dev >= 0 && cur_dev < kMaxDevices) configured_for[cur_dev].store((int)smem + 1);
   }
@@ -607,13 +632,13 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   if (work == 0) return XCT_OK;
   const int grid = work < sms * C::MINB ? work : sms * C::MINB;
   XCT_TRY_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int), st));
-  spmm_pipe_kernel<TX, ST><<<grid, C::NT, smem, st>>>(a);
+  spmm_pipe_kernel<TX, TW, ST><<<grid, C::NT, smem, st>>>(a);
   count_launch();
   XCT_TRY_CUDA(cudaGetLastError());
   return XCT_OK;
 }
 
-template <class TX>
+template <class TX, class TW>
 xct_status dispatch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   // the persistent form is built for staged rows of 32, 64 or 128 bytes
   // (16, 32 or 64 slices in 16 bits; 8, 16 or 32 in FP32)
@@ -623,9 +648,9 @@ xct_status dispatch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
       return XCT_ERR_INVALID;
     }
   switch (list[0].st * PBytes<TX>::v) {
-    case 128: return launch_pipe<TX, 128 / PBytes<TX>::v>(list, count, st);
-    case 64: return launch_pipe<TX, 64 / PBytes<TX>::v>(list, count, st);
-    case 32: return launch_pipe<TX, 32 / PBytes<TX>::v>(list, count, st);
+    case 128: return launch_pipe<TX, TW, 128 / PBytes<TX>::v>(list, count, st);
+    case 64: return launch_pipe<TX, TW, 64 / PBytes<TX>::v>(list, count, st);
+    case 32: return launch_pipe<TX, TW, 32 / PBytes<TX>::v>(list, count, st);
     default:
       set_error("persistent product: unsupported tile width %d", list[0].st);
       return XCT_ERR_UNSUPPORTED;
@@ -639,9 +664,16 @@ xct_status pipe_any(const SpmmArgs* list, int count, cudaStream_t s) {
       set_error("persistent product: products of one launch must share the storage type");
       return XCT_ERR_INVALID;
     }
-  if (t == XCT_F32) return dispatch_pipe<float>(list, count, s);
-  if (t == XCT_F16) return dispatch_pipe<__half>(list, count, s);
-  return dispatch_pipe<__nv_bfloat16>(list, count, s);
+  switch (t) {
+    case XCT_F32: return dispatch_pipe<float, float>(list, count, s);
+    case XCT_F16: return dispatch_pipe<__half, __half>(list, count, s);
+    case XCT_BF16: return dispatch_pipe<__nv_bfloat16, __nv_bfloat16>(list, count, s);
+    case XCT_F16A: return dispatch_pipe<float, __half>(list, count, s);
+    case XCT_BF16A: return dispatch_pipe<float, __nv_bfloat16>(list, count, s);
+    default:
+      set_error("persistent product: unknown storage type");
+      return XCT_ERR_INVALID;
+  }
 }
 
 }  // namespace
@@ -649,7 +681,7 @@ xct_status pipe_any(const SpmmArgs* list, int count, cudaStream_t s) {
 // The persistent form needs 16-byte lane vectors, staged rows of 32, 64 or
 // 128 bytes and two buffers in the shared memory of one of its CTAs.
 bool spmm_pipe_applies(const SpmmArgs& a) {
-  const int pixb = a.st * (a.storage == XCT_F32 ? 4 : 2);
+  const int pixb = a.st * (stages16(a.storage) ? 2 : 4);
   if ((pixb != 128 && pixb != 64 && pixb != 32) || !a.work || !a.err) return false;
   if (a.L->nblocks == 0) return false;
   return pipe_smem_bytes(a.L->cap, a.L->emax_slots, a.L->run_max, pixb,
@@ -671,7 +703,7 @@ bool spmm_pipe_multi_applies(const SpmmArgs* list, int count) {
     emax = emax > list[i].L->emax_slots ? emax : list[i].L->emax_slots;
     rmax = rmax > list[i].L->run_max ? rmax : list[i].L->run_max;
   }
-  const int pixb = list[0].st * (list[0].storage == XCT_F32 ? 4 : 2);
+  const int pixb = list[0].st * (stages16(list[0].storage) ? 2 : 4);
   return pipe_smem_bytes(cap, emax, rmax, pixb, list[0].storage == XCT_F32 ? 8 : 4, nullptr,
                          nullptr, nullptr) <= pipe_cta_smem_max(pipe_minb(pixb));
 }

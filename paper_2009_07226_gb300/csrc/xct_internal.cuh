@@ -76,6 +76,13 @@ struct Arena {
   }
 };
 
+// storage forms: 16-bit matrix values; 16-bit (normalised) staged slices;
+// binary16 (rather than bfloat16) values
+inline bool matrix16(xct_dtype t) { return t != XCT_F32; }
+inline bool stages16(xct_dtype t) { return t == XCT_F16 || t == XCT_BF16; }
+inline bool half_values(xct_dtype t) { return t == XCT_F16 || t == XCT_F16A; }
+inline bool valid_storage(int t) { return t >= XCT_F32 && t <= XCT_BF16A; }
+
 // ---------------------------------------------------------------------------
 // kernel layout of one matrix (A or A^T)
 // ---------------------------------------------------------------------------

@@ -19,12 +19,13 @@ LIB_PATH = os.path.join(_HERE, "libxct.so")
 
 XCT_OK, XCT_ERR_INVALID, XCT_ERR_OOM, XCT_ERR_CUDA = 0, 1, 2, 3
 XCT_ERR_TIMEOUT, XCT_ERR_BREAKDOWN, XCT_ERR_UNSUPPORTED = 4, 5, 6
-XCT_F32, XCT_F16, XCT_BF16 = 0, 1, 2
+XCT_F32, XCT_F16, XCT_BF16, XCT_F16A, XCT_BF16A = 0, 1, 2, 3, 4
 XCT_PLAN_KEEP_F64 = 1
 XCT_CGLS_X0, XCT_CGLS_NO_GRAPH, XCT_CGLS_TIMING = 1, 2, 4
 XCT_EXPORT_A_F64, XCT_EXPORT_AT_F64, XCT_EXPORT_A_STORED, XCT_EXPORT_AT_STORED = 0, 1, 2, 3
 
-STORAGE = {"f32": XCT_F32, "f16": XCT_F16, "bf16": XCT_BF16}
+STORAGE = {"f32": XCT_F32, "f16": XCT_F16, "bf16": XCT_BF16, "f16a": XCT_F16A,
+           "bf16a": XCT_BF16A}
 _STATUS = {0: "XCT_OK", 1: "XCT_ERR_INVALID", 2: "XCT_ERR_OOM", 3: "XCT_ERR_CUDA",
            4: "XCT_ERR_TIMEOUT", 5: "XCT_ERR_BREAKDOWN", 6: "XCT_ERR_UNSUPPORTED"}
 

@@ -65,13 +65,13 @@ def test_hilbert_orderings(xct, n, m, nd, off, sp, tile):
     assert np.array_equal(ray, oracle.hilbert_order(nd, m, T, "col"))
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16", "f16a", "bf16a"])
 @pytest.mark.parametrize("n,m,nd,off,sp,tile", [GEOMS[1], GEOMS[2], GEOMS[3], GEOMS[6]])
 def test_packed_values_are_rounded_matrix(xct, storage, n, m, nd, off, sp, tile):
     g, a, at = _oracle(n, m, nd, off, sp)
     rnd = {"f32": lambda v: v.astype(np.float32).astype(np.float64),
            "f16": lambda v: oracle.round_f16(v * 2.0 ** 15) * 2.0 ** -15,
-           "bf16": oracle.round_bf16}[storage]
+           "bf16": oracle.round_bf16}[storage.rstrip("a")]
     with xct.Plan(n, m, nd, storage, cos_sin=g.table(), det_offset=off, det_spacing=sp,
                   hilbert_tile=tile) as p:
         for what, ref in ((xct.XCT_EXPORT_A_STORED, a), (xct.XCT_EXPORT_AT_STORED, at)):

@@ -85,7 +85,7 @@ def test_f32_products_vs_oracle(xct, n, m, nd, S, off, sp):
         _check(xo.cpu().numpy(), oracle.backproject(at, y32), oracle.backproject(absat, np.abs(y32)))
 
 
-@pytest.mark.parametrize("kind", ["f16", "bf16"])
+@pytest.mark.parametrize("kind", ["f16", "bf16", "f16a", "bf16a"])
 @pytest.mark.parametrize("n,m,nd,S,off,sp", [CASES[1], CASES[2], CASES[3], CASES[6], CASES[7], CASES[9]])
 def test_mixed_products_vs_oracle_model(xct, kind, n, m, nd, S, off, sp):
     g, a, at, absa, absat = _setup(n, m, nd, off, sp)
@@ -103,11 +103,13 @@ def test_mixed_products_vs_oracle_model(xct, kind, n, m, nd, S, off, sp):
     y32 = y.astype(np.float32).astype(np.float64)
     for got, mat, absm, v in ((yo, a, absa, x32), (xo, at, absat, y32)):
         got = got.cpu().numpy().reshape(S, -1)
-        model = oracle.mixed_project(mat, v, kind)
+        # f16a / bf16a: only the matrix is 16-bit, the slices stay FP32
+        model = (oracle.mixed_project(mat, v, kind) if kind in ("f16", "bf16")
+                 else oracle.matrix16_project(mat, v, kind[:-1]))
         _check(got, model, oracle.project(absm, np.abs(v)))
         # against FP64: per slice, within the 16-bit unit roundoff
         exact = oracle.project(mat, v)
-        u = 2.0 ** -11 if kind == "f16" else 2.0 ** -8
+        u = 2.0 ** -11 if kind.startswith("f16") else 2.0 ** -8
         for s in range(S):
             nrm = np.linalg.norm(exact[s])
             if nrm > 0:

@@ -225,6 +225,31 @@ def test_mixed_product_error_scale():
         assert u / 100 < err < u, (kind, err)
 
 
+def test_matrix16_product_pins():
+    """Matrix-only rounding: exact for unit chords and any single-precision
+    input; equal to the mixed product when the inputs are already 16-bit
+    representable after normalisation; otherwise between the exact product
+    and the mixed one, with an error at the matrix's unit roundoff."""
+    n = 8
+    g0 = oracle.Geometry(n=n, m=1, nd=n, cos_sin=np.array([[1.0, 0.0]]))
+    a0 = oracle.siddon_csr(g0)
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal((3, n * n)).astype(np.float32).astype(np.float64)
+    for kind in ("f16", "bf16"):
+        np.testing.assert_array_equal(oracle.matrix16_project(a0, x, kind), oracle.project(a0, x))
+    g = oracle.Geometry(n=32, m=24, nd=32, cos_sin=inputs.angle_table(24))
+    a = oracle.siddon_csr(g)
+    xr = rng.integers(1, 64, size=(2, g.npix)).astype(np.float64) / 64.0
+    xf = rng.uniform(0.1, 1.0, size=(2, g.npix)).astype(np.float32).astype(np.float64)
+    y = oracle.project(a, xf)
+    for kind, u in (("f16", 2.0 ** -11), ("bf16", 2.0 ** -8)):
+        np.testing.assert_allclose(oracle.matrix16_project(a, xr, kind), oracle.mixed_project(a, xr, kind),
+                                   rtol=1e-15, atol=0)
+        em = np.linalg.norm(oracle.matrix16_project(a, xf, kind) - y) / np.linalg.norm(y)
+        ex = np.linalg.norm(oracle.mixed_project(a, xf, kind) - y) / np.linalg.norm(y)
+        assert u / 100 < em < u and em < ex, (kind, em, ex)
+
+
 # --------------------------------------------------------------------------
 # smoothed total variation
 # --------------------------------------------------------------------------
