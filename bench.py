@@ -236,6 +236,7 @@ def run_ours(args):
     def timed(kind, steps):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         tp = tb = to = 0.0
+        parts = {"stage": 0.0, "vector": 0.0, "scalar": 0.0}
         npj = nbp = 0
         barrier()
         launches0 = xct.xct_launch_count()
@@ -246,14 +247,18 @@ def run_ours(args):
             tp += st["t_project_ms"]
             tb += st["t_backproject_ms"]
             to += st["t_other_ms"]
+            for k in parts:
+                parts[k] += st[f"t_{k}_ms"]
             npj += st["n_project"]
             nbp += st["n_backproject"]
         ev1.record(stream)
         barrier()
         launches = xct.xct_launch_count() - launches0
         ms = shard.max_over_ranks(ev0.elapsed_time(ev1) / steps, dev)
+        timed.parts[kind] = {k: v / steps for k, v in parts.items()}
         return ms, tp / max(npj, 1), tb / max(nbp, 1), to / steps, launches
 
+    timed.parts = {}
     for kind in ("f16", "f32", "f16a"):
         for _ in range(args.warmup):
             step(kind)
@@ -354,6 +359,7 @@ def run_ours(args):
                                "rel_err_vs_fp32": rel_a},
         "rel_err_projection_mixed_vs_fp32": proj_err,
         "graph_ms_per_step": graph_ms,
+        "other_f16_ms_per_step": timed.parts["f16"],
         "kernel_ms": {"project_f16": proj16, "backproject_f16": back16, "other_f16_per_step": other16,
                       "project_f32": proj32, "backproject_f32": back32, "other_f32_per_step": other32},
         "roofline": {

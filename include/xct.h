@@ -224,6 +224,9 @@ typedef struct {
   /* filled by the last xct_cgls run with XCT_CGLS_TIMING: */
   double t_project_ms, t_backproject_ms, t_other_ms;
   int64_t n_project, n_backproject;
+  /* the parts of t_other_ms: 16-bit staging of the product inputs, vector
+     updates (and layout conversions), FP64 scalar kernels */
+  double t_stage_ms, t_vector_ms, t_scalar_ms;
 } xct_stats;
 
 xct_status xct_plan_stats(xct_plan_t plan, xct_stats* out);

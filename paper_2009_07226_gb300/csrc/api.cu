@@ -147,12 +147,14 @@ struct CglsBufs {
   CglsScalars sc;
 };
 
-// the staging pre-pass counts as vector work (kind 2), the product kernel as
-// projection (0) or back projection (1)
+// timed phases: projection (0), back projection (1), 16-bit staging of a
+// product input (2), vector updates (3), FP64 scalars (4)
+constexpr int kPhProject = 0, kPhBackproject = 1, kPhStage = 2, kPhVector = 3, kPhScalar = 4;
+
 xct_status spmm_timed(const SpmmArgs& a, int kind, PhaseTimer* tm, cudaStream_t s) {
-  if (tm) XCT_TRY(tm->begin(2));
+  if (tm) XCT_TRY(tm->begin(kPhStage));
   XCT_TRY(spmm_stage(a, s));
-  if (tm) XCT_TRY(tm->end(2));
+  if (tm) XCT_TRY(tm->end(kPhStage));
   if (tm) XCT_TRY(tm->begin(kind));
   XCT_TRY(spmm_run(a, s));
   if (tm) XCT_TRY(tm->end(kind));
@@ -186,23 +188,29 @@ xct_status enqueue_cgls(Plan& p, const float* yd, float* xd, int S, int st, int 
     SpmmArgs a{&p.lat, B.R, B.Sv, st, ntiles, p.storage, k, B.sc.max_r, B.gpart, B.h_ray, B.work, p.err};
     XCT_TRY(spmm_timed(a, 1, tm, s));
   }
+  if (tm) XCT_TRY(tm->begin(kPhScalar));
   XCT_TRY(cgls_init_scalars(B.gpart, nb_at, B.rpart, B.sc, B.log, S_pad, s));
-  if (tm) XCT_TRY(tm->begin(2));
+  if (tm) XCT_TRY(tm->end(kPhScalar));
+  if (tm) XCT_TRY(tm->begin(kPhVector));
   XCT_TRY(cgls_update_p(B.P, B.Sv, npix, st, ntiles, B.sc, s));
-  if (tm) XCT_TRY(tm->end(2));
+  if (tm) XCT_TRY(tm->end(kPhVector));
   for (int it = 1; it <= iters; ++it) {
     SpmmArgs ap{&p.la, B.P, B.Q, st, ntiles, p.storage, k, B.sc.max_p, B.dpart, B.h_pix, B.work, p.err};
     XCT_TRY(spmm_timed(ap, 0, tm, s));
-    if (tm) XCT_TRY(tm->begin(2));
+    if (tm) XCT_TRY(tm->begin(kPhScalar));
     XCT_TRY(cgls_alpha(B.dpart, spmm_dot_count(ap), B.sc, S_pad, s));
+    if (tm) XCT_TRY(tm->end(kPhScalar));
+    if (tm) XCT_TRY(tm->begin(kPhVector));
     XCT_TRY(cgls_update_xr(B.X, B.P, npix, B.R, B.Q, nray, st, ntiles, B.sc, B.rpart, s));
-    if (tm) XCT_TRY(tm->end(2));
+    if (tm) XCT_TRY(tm->end(kPhVector));
     SpmmArgs at{&p.lat, B.R, B.Sv, st, ntiles, p.storage, k, B.sc.max_r, B.gpart, B.h_ray, B.work, p.err};
     XCT_TRY(spmm_timed(at, 1, tm, s));
-    if (tm) XCT_TRY(tm->begin(2));
+    if (tm) XCT_TRY(tm->begin(kPhScalar));
     XCT_TRY(cgls_beta(B.gpart, nb_at, B.rpart, B.sc, B.log + (size_t)it * S_pad * 2, S_pad, s));
+    if (tm) XCT_TRY(tm->end(kPhScalar));
+    if (tm) XCT_TRY(tm->begin(kPhVector));
     XCT_TRY(cgls_update_p(B.P, B.Sv, npix, st, ntiles, B.sc, s));
-    if (tm) XCT_TRY(tm->end(2));
+    if (tm) XCT_TRY(tm->end(kPhVector));
   }
   XCT_TRY(to_natural(B.X, xd, p.pix_inv, npix, S, st, ntiles, s));
   return XCT_OK;
@@ -294,19 +302,22 @@ xct_status cgls_impl(Plan& p, const float* y, float* x, int32_t S, int32_t iters
                          timing ? &tm : nullptr));
     if (timing) {
       XCT_TRY_CUDA(cudaStreamSynchronize(us));
-      double t[3] = {0, 0, 0};
-      int64_t n[3] = {0, 0, 0};
+      double t[5] = {0, 0, 0, 0, 0};
+      int64_t n[5] = {0, 0, 0, 0, 0};
       for (auto& e : tm.ev) {
         float ms = 0;
         XCT_TRY_CUDA(cudaEventElapsedTime(&ms, e.second.first, e.second.second));
         t[e.first] += ms;
         n[e.first] += 1;
       }
-      p.stats.t_project_ms = t[0];
-      p.stats.t_backproject_ms = t[1];
-      p.stats.t_other_ms = t[2];
-      p.stats.n_project = n[0];
-      p.stats.n_backproject = n[1];
+      p.stats.t_project_ms = t[kPhProject];
+      p.stats.t_backproject_ms = t[kPhBackproject];
+      p.stats.t_stage_ms = t[kPhStage];
+      p.stats.t_vector_ms = t[kPhVector];
+      p.stats.t_scalar_ms = t[kPhScalar];
+      p.stats.t_other_ms = t[kPhStage] + t[kPhVector] + t[kPhScalar];
+      p.stats.n_project = n[kPhProject];
+      p.stats.n_backproject = n[kPhBackproject];
     }
   }
   if (resid) {

@@ -281,8 +281,19 @@ __global__ void loss_kernel(const double* __restrict__ rpart, int nbr, const dou
 
 __device__ double block_reduce_fixed(const double* part, int n) {
   __shared__ double sh[kVecThreads];
-  double a = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a += part[i];
+  // four independent accumulators per thread (loads and adds overlap),
+  // combined in a fixed order
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  const int step = blockDim.x;
+  int i = threadIdx.x;
+  for (; i + 3 * step < n; i += 4 * step) {
+    a0 += part[i];
+    a1 += part[i + step];
+    a2 += part[i + 2 * step];
+    a3 += part[i + 3 * step];
+  }
+  for (; i < n; i += step) a0 += part[i];
+  double a = (a0 + a1) + (a2 + a3);
   sh[threadIdx.x] = a;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {

@@ -52,7 +52,9 @@ class xct_stats(ctypes.Structure):
                 ("bytes_a", ctypes.c_int64), ("bytes_at", ctypes.c_int64),
                 ("plan_ms", ctypes.c_double), ("t_project_ms", ctypes.c_double),
                 ("t_backproject_ms", ctypes.c_double), ("t_other_ms", ctypes.c_double),
-                ("n_project", ctypes.c_int64), ("n_backproject", ctypes.c_int64)]
+                ("n_project", ctypes.c_int64), ("n_backproject", ctypes.c_int64),
+                ("t_stage_ms", ctypes.c_double), ("t_vector_ms", ctypes.c_double),
+                ("t_scalar_ms", ctypes.c_double)]
 
 
 class xct_job(ctypes.Structure):
