@@ -85,6 +85,10 @@ typedef struct xct_plan_s* xct_plan_t;
 /* Plan flags. */
 #define XCT_PLAN_KEEP_F64 1u  /* keep the FP64 CSR of A and A^T on the device
                                  for xct_plan_export (12 bytes per entry each) */
+#define XCT_PLAN_AUTOTUNE 2u  /* choose each matrix's stage capacity -- the
+                                 pixels (of A) or rays (of A^T) a CTA stages at
+                                 a time -- by timing its product on the widest
+                                 slice tile (about 3x the layout time) */
 
 /*
  * xct_plan -- build the memoized operator (Sec. II-B memoization; Sec. III-A1
@@ -215,8 +219,8 @@ typedef struct {
   int64_t n_rays, n_pix, nnz;        /* rows of A, columns of A, entries */
   int32_t storage;                   /* xct_dtype */
   int32_t rows_per_block;            /* rows of one thread block */
-  int32_t stage_capacity;            /* pixels (or rays) per staged buffer */
-  int32_t reserved;
+  int32_t stage_capacity;            /* pixels of A per staged buffer */
+  int32_t stage_capacity_at;         /* rays of A^T per staged buffer */
   int64_t stages_a, stages_at;       /* staged buffers over all blocks */
   int64_t slots_a, slots_at;         /* stored entries incl. padding */
   int64_t bytes_a, bytes_at;         /* device bytes of each packed form */

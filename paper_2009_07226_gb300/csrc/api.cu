@@ -431,7 +431,7 @@ xct_status xct_plan(const xct_geometry* g, xct_dtype storage, uint32_t flags, vo
     set_error("storage %d is not XCT_F32, XCT_F16, XCT_BF16, XCT_F16A or XCT_BF16A", (int)storage);
     return XCT_ERR_INVALID;
   }
-  if (flags & ~XCT_PLAN_KEEP_F64) {
+  if (flags & ~(XCT_PLAN_KEEP_F64 | XCT_PLAN_AUTOTUNE)) {
     set_error("unknown plan flags 0x%x", flags);
     return XCT_ERR_INVALID;
   }

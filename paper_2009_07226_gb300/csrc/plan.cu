@@ -888,6 +888,47 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
 // orchestration
 // ---------------------------------------------------------------------------
 
+// Time one product on layout L at the widest slice tile of the plan's
+// storage (inputs zero: the work does not depend on the values), after one
+// warm-up; the mean of two launches in milliseconds.
+xct_status time_product(const Layout& L, Plan& p, cudaStream_t s, double* ms_out) {
+  const int st = pick_slices_per_tile(p.storage, 64);
+  Arena ar(s);
+  float *xi, *yi;
+  uint16_t* h = nullptr;
+  uint32_t* mx;
+  double* dot;
+  int* work;
+  XCT_TRY(ar.get(&xi, (size_t)L.ncols * st));
+  XCT_TRY(ar.get(&yi, (size_t)L.nrows * st));
+  if (stages16(p.storage)) XCT_TRY(ar.get(&h, (size_t)L.ncols * st));
+  XCT_TRY(ar.get(&mx, (size_t)st));
+  XCT_TRY(ar.get(&dot, (size_t)st * std::max(L.nblocks, 1)));
+  XCT_TRY(ar.get(&work, 1));
+  XCT_TRY_CUDA(cudaMemsetAsync(xi, 0, sizeof(float) * L.ncols * st, s));
+  XCT_TRY_CUDA(cudaMemsetAsync(mx, 0, sizeof(uint32_t) * st, s));
+  SpmmArgs a{&L, xi, yi, st, 1, p.storage, p.mat_scale_exp, mx, dot, h, work, p.err};
+  cudaEvent_t e0, e1;
+  XCT_TRY_CUDA(cudaEventCreate(&e0));
+  XCT_TRY_CUDA(cudaEventCreate(&e1));
+  xct_status r = spmm(a, s);
+  if (r == XCT_OK) cudaEventRecord(e0, s);
+  for (int k = 0; k < 2 && r == XCT_OK; ++k) r = spmm(a, s);
+  if (r == XCT_OK) cudaEventRecord(e1, s);
+  float ms = 0.0f;
+  cudaError_t ce = cudaEventSynchronize(e1);
+  if (ce == cudaSuccess && r == XCT_OK) ce = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  XCT_TRY(r);
+  if (ce != cudaSuccess) {
+    set_error("stage capacity timing failed: %s", cudaGetErrorString(ce));
+    return XCT_ERR_CUDA;
+  }
+  *ms_out = ms / 2.0;
+  return XCT_OK;
+}
+
 xct_status build_plan(Plan& p, cudaStream_t s) {
   auto t0 = std::chrono::steady_clock::now();
   const xct_geometry& g = p.g;
@@ -945,29 +986,54 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
   XCT_TRY(f64.get(&tval, p.nnz));
   XCT_TRY(transpose(rowptr, col, val, p.nray, p.npix, p.nnz, colptr, trow, tval, s));
 
-  // Stage capacity: the pipeline buffers (128-byte staged rows plus the
-  // stage's packed entries) must fit in shared memory; a layout whose largest
-  // stage does not fit is rebuilt with a smaller capacity.
+  // Stage capacity of each matrix: the pipeline buffers (128-byte staged
+  // rows plus the stage's packed entries) must fit in shared memory; a layout
+  // whose largest stage does not fit is rebuilt with a smaller capacity.
+  // With XCT_PLAN_AUTOTUNE the capacity is also chosen by timing the
+  // product on the widest slice tile among a few candidates.
   CsrView ma{rowptr, col, val, p.nray, p.npix};
   CsrView mt{colptr, trow, tval, p.npix, p.nray};
-  int32_t cap = p.storage == XCT_F32 ? kPipeCap32 : kPipeCap16;
-  for (int attempt = 0;; ++attempt) {
-    Arena la_mem(s), lat_mem(s);
-    Layout la, lat;
-    XCT_TRY(build_layout(ma, p.nnz, p.storage, cap, la, la_mem, s));
-    XCT_TRY(build_layout(mt, p.nnz, p.storage, cap, lat, lat_mem, s));
-    const bool fits = kPipeBufs * pipe_buffer_bytes(la, 128) <= kPipeSmemLimit &&
-                      kPipeBufs * pipe_buffer_bytes(lat, 128) <= kPipeSmemLimit;
-    if (fits || attempt == 3 || cap <= 64) {
-      p.la = la;
-      p.lat = lat;
-      la_mem.move_to(keep);
-      lat_mem.move_to(keep);
-      break;
+  const int32_t cap0 = p.storage == XCT_F32 ? kPipeCap32 : kPipeCap16;
+  auto fitted = [&](const CsrView& m, int32_t cap, Layout& L, Arena& mem) -> xct_status {
+    for (int attempt = 0;; ++attempt) {
+      Arena lm(s);
+      Layout t;
+      XCT_TRY(build_layout(m, p.nnz, p.storage, cap, t, lm, s));
+      if (kPipeBufs * pipe_buffer_bytes(t, 128) <= kPipeSmemLimit || attempt == 3 || cap <= 64) {
+        L = t;
+        lm.move_to(mem);
+        return XCT_OK;
+      }
+      cap = (cap * 3 / 4) & ~3;   // multiple of 4: stage lists stay 16-byte aligned
     }
-    cap = (cap * 3 / 4) & ~3;   // multiple of 4: stage lists stay 16-byte aligned
+  };
+  for (int which = 0; which < 2; ++which) {
+    const CsrView& m = which == 0 ? ma : mt;
+    Layout& out = which == 0 ? p.la : p.lat;
+    if (!(p.flags & XCT_PLAN_AUTOTUNE)) {
+      Arena mem(s);
+      XCT_TRY(fitted(m, cap0, out, mem));
+      mem.move_to(keep);
+      continue;
+    }
+    double best_ms = 1e300;
+    Arena best_mem(s);
+    for (int32_t cand : {cap0, (cap0 * 4 / 5) & ~3, (cap0 * 3 / 5) & ~3}) {
+      Arena mem(s);
+      Layout L;
+      XCT_TRY(fitted(m, cand, L, mem));
+      double ms = 0.0;
+      XCT_TRY(time_product(L, p, s, &ms));
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_mem.release();
+        mem.move_to(best_mem);
+        out = L;
+      }
+    }
+    best_mem.move_to(keep);
   }
-  const int32_t cap_used = cap;
+  const int32_t cap_used = p.la.cap;
 
   if (p.flags & XCT_PLAN_KEEP_F64) {
     p.a_rowptr = rowptr; p.a_col = col; p.a_val = val;
@@ -987,6 +1053,7 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
   st.storage = p.storage;
   st.rows_per_block = kRowsPerBlock;
   st.stage_capacity = cap_used;
+  st.stage_capacity_at = p.lat.cap;
   st.stages_a = p.la.nstages;
   st.stages_at = p.lat.nstages;
   st.slots_a = p.la.nslots;

@@ -7,6 +7,7 @@ practice they are identical); stored 16-bit / 32-bit values equal the
 oracle's rounding of the FP64 values exactly."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from paper_2009_07226_gb300 import inputs
@@ -98,3 +99,34 @@ def test_plan_stats_are_consistent(xct):
     assert st["slots_a"] >= st["nnz"] and st["slots_at"] >= st["nnz"]
     assert st["bytes_a"] >= 4 * st["nnz"]
     assert st["plan_ms"] > 0
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_autotuned_stage_capacity(xct, storage):
+    """XCT_PLAN_AUTOTUNE picks each matrix's stage capacity by timing; the
+    layouts stay exact (stored values equal the rounding model) and the
+    products agree with the default plan's to the FP32 summation order (a
+    row's entries are summed stage by stage, so other stage boundaries
+    regroup them)."""
+    n, m, nd = 96, 128, 96
+    g, a, at = _oracle(n, m, nd, 0.0, 1.0)
+    cands = {"f32": (200, 160, 120), "f16": (280, 224, 168)}[storage]
+    with xct.Plan(n, m, nd, storage, cos_sin=g.table(), autotune=True) as pt, \
+            xct.Plan(n, m, nd, storage, cos_sin=g.table()) as pd:
+        st = pt.stats()
+        for cap in (st["stage_capacity"], st["stage_capacity_at"]):
+            # a candidate, or a candidate reduced until its buffers fit
+            assert any(cap <= c and cap % 4 == 0 for c in cands), cap
+        rnd = {"f32": lambda v: v.astype(np.float32).astype(np.float64),
+               "f16": lambda v: oracle.round_f16(v * 2.0 ** 15) * 2.0 ** -15}[storage]
+        for what, ref in ((xct.XCT_EXPORT_A_STORED, a), (xct.XCT_EXPORT_AT_STORED, at)):
+            rp, col, val = xct.xct_plan_export(pt.handle, what)
+            assert np.array_equal(rp, ref.rowptr) and np.array_equal(col, ref.col)
+            assert np.array_equal(val, rnd(ref.val))
+        gen = torch.Generator(device="cuda").manual_seed(3)
+        x = torch.rand((64, n, n), device="cuda", generator=gen)
+        y = torch.rand((64, m, nd), device="cuda", generator=gen)
+        for fn in ("project", "backproject"):
+            arg = x if fn == "project" else y
+            u, v = getattr(pt, fn)(arg), getattr(pd, fn)(arg)
+            assert float((u - v).norm() / v.norm()) <= 1e-6, fn
