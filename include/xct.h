@@ -146,6 +146,27 @@ xct_status xct_backproject(xct_plan_t plan, const float* y, float* x,
 xct_status xct_cgls(xct_plan_t plan, const float* y, float* x, int32_t S,
                     int32_t iters, uint32_t flags, double* resid, void* stream);
 
+/* CGLS state flags (xct_cgls_state). */
+#define XCT_CGLS_SAVE 32u    /* write the state after the last iteration */
+#define XCT_CGLS_RESUME 64u  /* start from the state instead of x0 / zero */
+
+/*
+ * xct_cgls_state -- xct_cgls with an exact checkpoint: with XCT_CGLS_SAVE
+ * the state after the last iteration (per slice x, r, p in natural layouts,
+ * the FP64 gamma = ||A^T r||^2 and the stop flag, and the iteration count)
+ * is written to `state`; with XCT_CGLS_RESUME the solve starts from it (y
+ * and x0 are not read) and continues exactly as the uninterrupted solve
+ * would: k iterations, save, then m iterations from the state give the x
+ * and residual log of k + m iterations bit for bit (same plan and S).  Both
+ * flags may be set (continue and save again).  state: host or device,
+ * xct_cgls_state_bytes(plan, S) bytes, owned by the caller; resid[0] of a
+ * resumed solve is the saved iteration's entry.  XCT_ERR_INVALID for a
+ * state of another plan or slice count.  The paper has no counterpart.
+ */
+int64_t xct_cgls_state_bytes(xct_plan_t plan, int32_t S);
+xct_status xct_cgls_state(xct_plan_t plan, const float* y, float* x, int32_t S, int32_t iters,
+                          uint32_t flags, double* resid, void* state, void* stream);
+
 /*
  * xct_tv -- smoothed total variation, the regulariser R(x) of Eq. 1 as this
  * library reads it: TV_eps(x_s) = sum_{i,j} sqrt(dx^2 + dy^2 + eps^2) per

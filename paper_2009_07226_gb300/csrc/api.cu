@@ -147,6 +147,37 @@ struct CglsBufs {
   CglsScalars sc;
 };
 
+// A saved CGLS state in device memory (sections of one buffer; layout in
+// xct_vec.cuh).
+struct CglsState {
+  CglsStateHeader* hdr = nullptr;
+  double* gamma = nullptr;
+  int32_t* active = nullptr;
+  float *x = nullptr, *r = nullptr, *p = nullptr;
+};
+
+size_t state_bytes(int64_t npix, int64_t nray, int S) {
+  const size_t act = ((size_t)S * 4 + 7) / 8 * 8;
+  return sizeof(CglsStateHeader) + (size_t)S * 8 + act + (size_t)S * (2 * npix + nray) * 4;
+}
+
+CglsState state_view(unsigned char* base, int64_t npix, int64_t nray, int S) {
+  CglsState v;
+  size_t o = 0;
+  v.hdr = reinterpret_cast<CglsStateHeader*>(base);
+  o += sizeof(CglsStateHeader);
+  v.gamma = reinterpret_cast<double*>(base + o);
+  o += (size_t)S * 8;
+  v.active = reinterpret_cast<int32_t*>(base + o);
+  o += ((size_t)S * 4 + 7) / 8 * 8;
+  v.x = reinterpret_cast<float*>(base + o);
+  o += (size_t)S * npix * 4;
+  v.r = reinterpret_cast<float*>(base + o);
+  o += (size_t)S * nray * 4;
+  v.p = reinterpret_cast<float*>(base + o);
+  return v;
+}
+
 // timed phases: projection (0), back projection (1), 16-bit staging of a
 // product input (2), vector updates (3), FP64 scalars (4)
 constexpr int kPhProject = 0, kPhBackproject = 1, kPhStage = 2, kPhVector = 3, kPhScalar = 4;
@@ -163,37 +194,52 @@ xct_status spmm_timed(const SpmmArgs& a, int kind, PhaseTimer* tm, cudaStream_t 
 
 // Enqueue the whole solve on stream s (graph-capturable: no host syncs).
 xct_status enqueue_cgls(Plan& p, const float* yd, float* xd, int S, int st, int ntiles, int iters,
-                        bool x0, CglsBufs& B, cudaStream_t s, PhaseTimer* tm) {
+                        bool x0, CglsBufs& B, cudaStream_t s, PhaseTimer* tm,
+                        const CglsState* resume = nullptr, const CglsState* save = nullptr,
+                        int iters_before = 0) {
   const int S_pad = st * ntiles;
   const int64_t npix = p.npix, nray = p.nray;
   const int k = p.mat_scale_exp;
-  XCT_TRY_CUDA(cudaMemsetAsync(B.sc.max_r, 0, sizeof(uint32_t) * S_pad, s));
-  XCT_TRY(to_internal(yd, B.R, p.ray_inv, nray, S, st, ntiles, B.sc.max_r, s));
-  if (x0) {
-    XCT_TRY_CUDA(cudaMemsetAsync(B.max_x, 0, sizeof(uint32_t) * S_pad, s));
-    XCT_TRY(to_internal(xd, B.X, p.pix_inv, npix, S, st, ntiles, B.max_x, s));
-    SpmmArgs a{&p.la, B.X, B.Q, st, ntiles, p.storage, k, B.max_x, nullptr, B.h_pix, B.work, p.err};
-    XCT_TRY(spmm_timed(a, 0, tm, s));
-    XCT_TRY_CUDA(cudaMemsetAsync(B.sc.max_r, 0, sizeof(uint32_t) * S_pad, s));
-    XCT_TRY(cgls_residual(B.R, B.Q, nray, st, ntiles, B.sc.max_r, B.rpart, s));
-  } else {
-    XCT_TRY_CUDA(cudaMemsetAsync(B.X, 0, sizeof(float) * npix * S_pad, s));
-    XCT_TRY(cgls_residual(B.R, nullptr, nray, st, ntiles, B.sc.max_r, B.rpart, s));
-  }
-  XCT_TRY_CUDA(cudaMemsetAsync(B.P, 0, sizeof(float) * npix * S_pad, s));
   const SpmmArgs probe_at{&p.lat, B.R, B.Sv, st, ntiles, p.storage, k, B.sc.max_r, B.gpart,
                           B.h_ray, B.work, p.err};
   const int nb_at = spmm_dot_count(probe_at);
-  {
-    SpmmArgs a{&p.lat, B.R, B.Sv, st, ntiles, p.storage, k, B.sc.max_r, B.gpart, B.h_ray, B.work, p.err};
-    XCT_TRY(spmm_timed(a, 1, tm, s));
+  if (resume) {
+    // x, r, p and the scalars of the saved iteration; its log entry
+    XCT_TRY_CUDA(cudaMemsetAsync(B.max_x, 0, sizeof(uint32_t) * S_pad, s));
+    XCT_TRY(to_internal(resume->x, B.X, p.pix_inv, npix, S, st, ntiles, B.max_x, s));
+    XCT_TRY_CUDA(cudaMemsetAsync(B.sc.max_p, 0, sizeof(uint32_t) * S_pad, s));
+    XCT_TRY(to_internal(resume->p, B.P, p.pix_inv, npix, S, st, ntiles, B.sc.max_p, s));
+    XCT_TRY_CUDA(cudaMemsetAsync(B.sc.max_r, 0, sizeof(uint32_t) * S_pad, s));
+    XCT_TRY(to_internal(resume->r, B.R, p.ray_inv, nray, S, st, ntiles, B.sc.max_r, s));
+    XCT_TRY_CUDA(cudaMemsetAsync(B.sc.max_r, 0, sizeof(uint32_t) * S_pad, s));
+    XCT_TRY(cgls_residual(B.R, nullptr, nray, st, ntiles, B.sc.max_r, B.rpart, s));
+    XCT_TRY(cgls_restore(resume->gamma, resume->active, S, B.rpart, B.sc, B.log, S_pad, s));
+  } else {
+    XCT_TRY_CUDA(cudaMemsetAsync(B.sc.max_r, 0, sizeof(uint32_t) * S_pad, s));
+    XCT_TRY(to_internal(yd, B.R, p.ray_inv, nray, S, st, ntiles, B.sc.max_r, s));
+    if (x0) {
+      XCT_TRY_CUDA(cudaMemsetAsync(B.max_x, 0, sizeof(uint32_t) * S_pad, s));
+      XCT_TRY(to_internal(xd, B.X, p.pix_inv, npix, S, st, ntiles, B.max_x, s));
+      SpmmArgs a{&p.la, B.X, B.Q, st, ntiles, p.storage, k, B.max_x, nullptr, B.h_pix, B.work, p.err};
+      XCT_TRY(spmm_timed(a, 0, tm, s));
+      XCT_TRY_CUDA(cudaMemsetAsync(B.sc.max_r, 0, sizeof(uint32_t) * S_pad, s));
+      XCT_TRY(cgls_residual(B.R, B.Q, nray, st, ntiles, B.sc.max_r, B.rpart, s));
+    } else {
+      XCT_TRY_CUDA(cudaMemsetAsync(B.X, 0, sizeof(float) * npix * S_pad, s));
+      XCT_TRY(cgls_residual(B.R, nullptr, nray, st, ntiles, B.sc.max_r, B.rpart, s));
+    }
+    XCT_TRY_CUDA(cudaMemsetAsync(B.P, 0, sizeof(float) * npix * S_pad, s));
+    {
+      SpmmArgs a{&p.lat, B.R, B.Sv, st, ntiles, p.storage, k, B.sc.max_r, B.gpart, B.h_ray, B.work, p.err};
+      XCT_TRY(spmm_timed(a, 1, tm, s));
+    }
+    if (tm) XCT_TRY(tm->begin(kPhScalar));
+    XCT_TRY(cgls_init_scalars(B.gpart, nb_at, B.rpart, B.sc, B.log, S_pad, s));
+    if (tm) XCT_TRY(tm->end(kPhScalar));
+    if (tm) XCT_TRY(tm->begin(kPhVector));
+    XCT_TRY(cgls_update_p(B.P, B.Sv, npix, st, ntiles, B.sc, s));
+    if (tm) XCT_TRY(tm->end(kPhVector));
   }
-  if (tm) XCT_TRY(tm->begin(kPhScalar));
-  XCT_TRY(cgls_init_scalars(B.gpart, nb_at, B.rpart, B.sc, B.log, S_pad, s));
-  if (tm) XCT_TRY(tm->end(kPhScalar));
-  if (tm) XCT_TRY(tm->begin(kPhVector));
-  XCT_TRY(cgls_update_p(B.P, B.Sv, npix, st, ntiles, B.sc, s));
-  if (tm) XCT_TRY(tm->end(kPhVector));
   for (int it = 1; it <= iters; ++it) {
     SpmmArgs ap{&p.la, B.P, B.Q, st, ntiles, p.storage, k, B.sc.max_p, B.dpart, B.h_pix, B.work, p.err};
     XCT_TRY(spmm_timed(ap, 0, tm, s));
@@ -213,6 +259,13 @@ xct_status enqueue_cgls(Plan& p, const float* yd, float* xd, int S, int st, int 
     if (tm) XCT_TRY(tm->end(kPhVector));
   }
   XCT_TRY(to_natural(B.X, xd, p.pix_inv, npix, S, st, ntiles, s));
+  if (save) {
+    XCT_TRY(to_natural(B.X, save->x, p.pix_inv, npix, S, st, ntiles, s));
+    XCT_TRY(to_natural(B.R, save->r, p.ray_inv, nray, S, st, ntiles, s));
+    XCT_TRY(to_natural(B.P, save->p, p.pix_inv, npix, S, st, ntiles, s));
+    const CglsStateHeader hdr{kCglsStateMagic, S, iters_before + iters, npix, nray};
+    XCT_TRY(cgls_save(B.sc, S, hdr, save->hdr, save->gamma, save->active, s));
+  }
   return XCT_OK;
 }
 
@@ -238,15 +291,36 @@ struct GraphGuard {
 };
 
 xct_status cgls_impl(Plan& p, const float* y, float* x, int32_t S, int32_t iters, uint32_t flags,
-                     double* resid, cudaStream_t us) {
+                     double* resid, void* state, cudaStream_t us) {
   const int st = pick_slices_per_tile(p.storage, S);
   const int ntiles = (S + st - 1) / st;
   const int S_pad = st * ntiles;
   Arena ar(us);
-  DevView yv, xv;
-  XCT_TRY(device_view(y, (size_t)S * p.nray, true, ar, us, yv));
+  DevView yv, xv, sv;
+  const bool resume = (flags & XCT_CGLS_RESUME) != 0, save = (flags & XCT_CGLS_SAVE) != 0;
+  XCT_TRY(device_view(y, (size_t)S * p.nray, !resume, ar, us, yv));
   const bool x0 = (flags & XCT_CGLS_X0) != 0;
-  XCT_TRY(device_view(x, (size_t)S * p.npix, x0, ar, us, xv));
+  XCT_TRY(device_view(x, (size_t)S * p.npix, x0 && !resume, ar, us, xv));
+  CglsState st_view{};
+  int iters_before = 0;
+  if (resume || save) {
+    const size_t nbytes = state_bytes(p.npix, p.nray, S);
+    XCT_TRY(device_view(static_cast<const float*>(state), nbytes / 4, resume, ar, us, sv));
+    st_view = state_view(reinterpret_cast<unsigned char*>(sv.dev), p.npix, p.nray, S);
+    if (resume) {
+      CglsStateHeader h{};
+      XCT_TRY_CUDA(cudaMemcpyAsync(&h, st_view.hdr, sizeof(h), cudaMemcpyDeviceToHost, us));
+      XCT_TRY_CUDA(cudaStreamSynchronize(us));
+      if (h.magic != kCglsStateMagic || h.S != S || h.npix != p.npix || h.nray != p.nray ||
+          h.iters_done < 0) {
+        set_error("the CGLS state does not belong to this plan and slice count");
+        return XCT_ERR_INVALID;
+      }
+      iters_before = h.iters_done;
+    }
+  }
+  const CglsState* resume_v = resume ? &st_view : nullptr;
+  const CglsState* save_v = save ? &st_view : nullptr;
   CglsBufs B{};
   XCT_TRY(ar.get(&B.X, (size_t)p.npix * S_pad));
   XCT_TRY(ar.get(&B.P, (size_t)p.npix * S_pad));
@@ -283,7 +357,8 @@ xct_status cgls_impl(Plan& p, const float* y, float* x, int32_t S, int32_t iters
     XCT_TRY_CUDA(cudaEventRecord(e0.e, us));
     XCT_TRY_CUDA(cudaStreamWaitEvent(cs.s, e0.e, 0));
     XCT_TRY_CUDA(cudaStreamBeginCapture(cs.s, cudaStreamCaptureModeThreadLocal));
-    xct_status st_enq = enqueue_cgls(p, yv.dev, xv.dev, S, st, ntiles, iters, x0, B, cs.s, nullptr);
+    xct_status st_enq = enqueue_cgls(p, yv.dev, xv.dev, S, st, ntiles, iters, x0, B, cs.s, nullptr,
+                                     resume_v, save_v, iters_before);
     cudaError_t ec = cudaStreamEndCapture(cs.s, &gg.g);
     if (st_enq != XCT_OK) return st_enq;
     if (ec != cudaSuccess) {
@@ -299,7 +374,7 @@ xct_status cgls_impl(Plan& p, const float* y, float* x, int32_t S, int32_t iters
     PhaseTimer tm;
     tm.s = us;
     XCT_TRY(enqueue_cgls(p, yv.dev, xv.dev, S, st, ntiles, iters, x0, B, us,
-                         timing ? &tm : nullptr));
+                         timing ? &tm : nullptr, resume_v, save_v, iters_before));
     if (timing) {
       XCT_TRY_CUDA(cudaStreamSynchronize(us));
       double t[5] = {0, 0, 0, 0, 0};
@@ -328,6 +403,9 @@ xct_status cgls_impl(Plan& p, const float* y, float* x, int32_t S, int32_t iters
   }
   if (xv.host)
     XCT_TRY_CUDA(cudaMemcpyAsync(x, xv.dev, sizeof(float) * S * p.npix, cudaMemcpyDeviceToHost, us));
+  if (save && sv.host)
+    XCT_TRY_CUDA(cudaMemcpyAsync(state, sv.dev, state_bytes(p.npix, p.nray, S),
+                                 cudaMemcpyDeviceToHost, us));
   std::vector<int> act0((size_t)S_pad);
   XCT_TRY_CUDA(cudaMemcpyAsync(act0.data(), B.sc.active0, sizeof(int) * S_pad,
                                cudaMemcpyDeviceToHost, us));
@@ -509,7 +587,26 @@ xct_status xct_cgls(xct_plan_t plan, const float* y, float* x, int32_t S, int32_
     return XCT_ERR_INVALID;
   }
   if (S == 0) return XCT_OK;
-  return cgls_impl(*plan, y, x, S, iters, flags, resid, static_cast<cudaStream_t>(stream));
+  return cgls_impl(*plan, y, x, S, iters, flags, resid, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int64_t xct_cgls_state_bytes(xct_plan_t plan, int32_t S) {
+  if (!plan || S < 1) return 0;
+  return (int64_t)state_bytes(plan->npix, plan->nray, S);
+}
+
+xct_status xct_cgls_state(xct_plan_t plan, const float* y, float* x, int32_t S, int32_t iters,
+                          uint32_t flags, double* resid, void* state, void* stream) {
+  XCT_TRY(check_plan(plan));
+  const uint32_t known = XCT_CGLS_X0 | XCT_CGLS_NO_GRAPH | XCT_CGLS_TIMING | XCT_CGLS_SAVE |
+                         XCT_CGLS_RESUME;
+  if (S < 1 || iters < 0 || !x || !state || (!y && !(flags & XCT_CGLS_RESUME)) || (flags & ~known) ||
+      !(flags & (XCT_CGLS_SAVE | XCT_CGLS_RESUME))) {
+    set_error("bad arguments (S = %d, iters = %d, flags 0x%x; SAVE or RESUME needed)", S, iters,
+              flags);
+    return XCT_ERR_INVALID;
+  }
+  return cgls_impl(*plan, y, x, S, iters, flags, resid, state, static_cast<cudaStream_t>(stream));
 }
 
 xct_status xct_plan_stats(xct_plan_t plan, xct_stats* out) {

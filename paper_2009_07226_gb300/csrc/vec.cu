@@ -359,6 +359,37 @@ __global__ void __launch_bounds__(kVecThreads) cgls_beta_kernel(const double* gp
   }
 }
 
+// resume from a saved state: gamma and the activity flags of the first S
+// slices (padding slices inactive), log[0] from the residual partials
+__global__ void __launch_bounds__(kVecThreads) cgls_restore_kernel(
+    const double* gamma_in, const int32_t* active_in, int S, const double* rpart, int nbr,
+    CglsScalars sc, double* log) {
+  const int gs = blockIdx.x;
+  const double rr = block_reduce_fixed(rpart + (size_t)gs * nbr, nbr);
+  if (threadIdx.x == 0) {
+    const double g = gs < S ? gamma_in[gs] : 0.0;
+    const int act = gs < S ? active_in[gs] : 0;
+    sc.gamma[gs] = g;
+    sc.active[gs] = act;
+    sc.active0[gs] = act;
+    sc.beta[gs] = 0.0;
+    if (log) {
+      log[(size_t)gs * 2] = sqrt(rr);
+      log[(size_t)gs * 2 + 1] = sqrt(g);
+    }
+  }
+}
+
+// save: gamma and the activity flags of the first S slices, and the header
+__global__ void cgls_save_kernel(const CglsScalars sc, int S, CglsStateHeader hdr,
+                                 CglsStateHeader* hdr_out, double* gamma_out, int32_t* active_out) {
+  for (int s = threadIdx.x; s < S; s += blockDim.x) {
+    gamma_out[s] = sc.gamma[s];
+    active_out[s] = sc.active[s];
+  }
+  if (threadIdx.x == 0) *hdr_out = hdr;
+}
+
 inline unsigned conv_blocks(int64_t rows) { return (unsigned)((rows + kConvRows - 1) / kConvRows); }
 
 }  // namespace
@@ -444,6 +475,25 @@ xct_status cgls_alpha(const double* dpart, int nbd, const CglsScalars& sc, int S
 xct_status cgls_beta(const double* gpart, int nbg, const double* rpart, const CglsScalars& sc,
                      double* log_k, int S_pad, cudaStream_t s) {
   cgls_beta_kernel<<<S_pad, kVecThreads, 0, s>>>(gpart, nbg, rpart, kVecBlocks, sc, log_k);
+  count_launch();
+  XCT_TRY_CUDA(cudaGetLastError());
+  return XCT_OK;
+}
+
+xct_status cgls_restore(const double* gamma_in, const int32_t* active_in, int S,
+                        const double* rpart, const CglsScalars& sc, double* log, int S_pad,
+                        cudaStream_t s) {
+  cgls_restore_kernel<<<S_pad, kVecThreads, 0, s>>>(gamma_in, active_in, S, rpart, kVecBlocks, sc,
+                                                     log);
+  count_launch();
+  XCT_TRY_CUDA(cudaGetLastError());
+  return XCT_OK;
+}
+
+xct_status cgls_save(const CglsScalars& sc, int S, const CglsStateHeader& hdr,
+                     CglsStateHeader* hdr_out, double* gamma_out, int32_t* active_out,
+                     cudaStream_t s) {
+  cgls_save_kernel<<<1, 256, 0, s>>>(sc, S, hdr, hdr_out, gamma_out, active_out);
   count_launch();
   XCT_TRY_CUDA(cudaGetLastError());
   return XCT_OK;

@@ -31,6 +31,23 @@ xct_status cgls_residual(float* r, const float* q, int64_t nray, int st, int nti
 xct_status vec_sub_sumsq(const float* q, const float* y, float* r, int64_t rows, int st,
                          int ntiles, uint32_t* max_r, double* rpart, cudaStream_t s);
 xct_status vec_loss(const double* rpart, const double* tv, int S, double* out, cudaStream_t s);
+// Header of a saved CGLS state (xct_cgls_state); followed by gamma[S]
+// (double), active[S] (int32, padded to 8 bytes), x[S][npix], r[S][nray],
+// p[S][npix] (float32, natural layouts).
+struct CglsStateHeader {
+  uint64_t magic;
+  int32_t S;
+  int32_t iters_done;
+  int64_t npix, nray;
+};
+constexpr uint64_t kCglsStateMagic = 0x31657461'74736778ull;  // "xgstate1"
+
+xct_status cgls_restore(const double* gamma_in, const int32_t* active_in, int S,
+                        const double* rpart, const CglsScalars& sc, double* log, int S_pad,
+                        cudaStream_t s);
+xct_status cgls_save(const CglsScalars& sc, int S, const CglsStateHeader& hdr,
+                     CglsStateHeader* hdr_out, double* gamma_out, int32_t* active_out,
+                     cudaStream_t s);
 xct_status cgls_init_scalars(const double* gpart, int nbg, const double* rpart,
                              const CglsScalars& sc, double* log, int S_pad, cudaStream_t s);
 xct_status cgls_alpha(const double* dpart, int nbd, const CglsScalars& sc, int S_pad,

@@ -22,6 +22,7 @@ XCT_ERR_TIMEOUT, XCT_ERR_BREAKDOWN, XCT_ERR_UNSUPPORTED = 4, 5, 6
 XCT_F32, XCT_F16, XCT_BF16, XCT_F16A, XCT_BF16A = 0, 1, 2, 3, 4
 XCT_PLAN_KEEP_F64, XCT_PLAN_AUTOTUNE = 1, 2
 XCT_CGLS_X0, XCT_CGLS_NO_GRAPH, XCT_CGLS_TIMING = 1, 2, 4
+XCT_CGLS_SAVE, XCT_CGLS_RESUME = 32, 64
 XCT_EXPORT_A_F64, XCT_EXPORT_AT_F64, XCT_EXPORT_A_STORED, XCT_EXPORT_AT_STORED = 0, 1, 2, 3
 
 STORAGE = {"f32": XCT_F32, "f16": XCT_F16, "bf16": XCT_BF16, "f16a": XCT_F16A,
@@ -99,6 +100,10 @@ _SIGNATURES = [
     ("xct_set_allocator", ctypes.c_int, [ALLOC_FN, FREE_FN, ctypes.c_void_p]),
     ("xct_last_error", ctypes.c_char_p, []),
     ("xct_launch_count", ctypes.c_int64, []),
+    ("xct_cgls_state_bytes", ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int32]),
+    ("xct_cgls_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                      ctypes.c_void_p]),
     ("xct_set_wait_limit", ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     ("xct_plan_check", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("xct_version", ctypes.c_char_p, []),
@@ -200,6 +205,18 @@ def xct_backproject(plan: int, y, x, S: int, stream=None) -> None:
 
 def xct_cgls(plan: int, y, x, S: int, iters: int, flags: int = 0, resid=None, stream=None) -> None:
     _check(lib().xct_cgls(plan, _ptr(y), _ptr(x), S, iters, flags, _ptr(resid), _stream(stream)))
+
+
+def xct_cgls_state_bytes(plan: int, S: int) -> int:
+    return lib().xct_cgls_state_bytes(plan, S)
+
+
+def xct_cgls_state(plan: int, y, x, S: int, iters: int, flags: int, state, resid=None,
+                   stream=None) -> None:
+    """CGLS with a checkpoint (flags include XCT_CGLS_SAVE and/or
+    XCT_CGLS_RESUME); state: uint8 buffer of xct_cgls_state_bytes bytes."""
+    _check(lib().xct_cgls_state(plan, _ptr(y), _ptr(x), S, iters, flags, _ptr(resid), _ptr(state),
+                                _stream(stream)))
 
 
 def xct_tv(x, n: int, S: int, eps: float, weight: float, grad=None, value=None, stream=None) -> None:
