@@ -2,24 +2,27 @@
 // Sec. III-B: input buffering, register reuse, output buffering, multi-stage
 // buffering; Sec. III-C: mixed precision).
 //
-// Two to four CTAs per SM (by the width of a staged row: 128, 64 or 32
-// bytes, i.e. 64 / 32 / 16 slices in 16 bits).  A producer warp takes blocks
-// of 64 rows from a work
-// counter and streams each stage of each block into one of two shared-memory
-// buffers with bulk asynchronous copies (cp.async.bulk) counted in bytes on
-// the buffer's mbarrier: one copy per contiguous run of the stage's staged
-// input rows (runs of consecutive Hilbert ids, about 11 rows on average; the
-// run list itself arrives one stage ahead by another bulk copy), one for the
-// stage's packed entries and one for its segment headers.  Sixteen consumer
-// warps compute from shared memory only and release the buffer through a
+// A producer warp takes blocks of 64 rows from a work counter and streams
+// each stage of each block into one of two shared-memory buffers with bulk
+// asynchronous copies (cp.async.bulk) counted in bytes on the buffer's
+// mbarrier: one copy per contiguous run of the stage's staged input rows
+// (runs of consecutive Hilbert ids, about 11 rows on average; the run list
+// itself arrives one stage ahead by another bulk copy), one for the stage's
+// packed entries and one for its segment headers.  The consumer warps (16
+// for 128-byte staged rows, 8 for 64-byte, 4 for 32-byte; 2, 3 or 4 CTAs per
+// SM) compute from shared memory only and release the buffer through a
 // second mbarrier; while they work on one stage the next one (possibly of the
 // next block) is already in flight.  The lane layout of the consumers is the
 // one of spmm.cu: a group of lanes holds different slices of one row, so every
 // shared-memory wavefront reads one contiguous staged row.
 //
-// Every wait is bounded (about two seconds of wall time); a wait that runs out
-// sets the caller's error flag, waits (bounded) for the copies this CTA has in
-// flight and returns.
+// Staged rows are 16-bit (normalised per slice) or FP32; matrix values are
+// FP32 or 16-bit (see PCfg and PFma).
+//
+// Every wait is bounded (xct_set_wait_limit, 2 s by default); a wait that
+// runs out sets the caller's error flag, waits (bounded) for the copies this
+// CTA has in flight and returns.  The consumers' block-end rendezvous is an
+// mbarrier too, so no warp can be left at an unbounded barrier.
 #include "xct_internal.cuh"
 
 namespace xct {

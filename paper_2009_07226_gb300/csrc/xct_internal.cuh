@@ -135,8 +135,9 @@ inline size_t pipe_buffer_bytes(const Layout& L, int pixb) {
 // stages ahead of the consumers)
 constexpr int kPipeBufs = XCT_PIPE_BUFS;
 static_assert(kPipeBufs == 2 || kPipeBufs == 3, "pipeline buffers");
-// shared memory one pipeline CTA may use for its buffers (the rest of its
-// 113 KB share goes to the barriers)
+// shared memory one pipeline CTA with 128-byte staged rows may use for its
+// buffers (two such CTAs share an SM; the rest of a CTA's 113 KB goes to the
+// barriers and run lists)
 constexpr size_t kPipeSmemLimit = 110 * 1024;
 // first stage capacity tried for each entry size (reduced until the buffers
 // fit in kPipeSmemLimit)
