@@ -678,6 +678,46 @@ def run_cusparse(args):
     print(json.dumps(out))
 
 
+def run_matfree(args):
+    """Memoized against matrix-free projection (Sec. II-B's argument for
+    memoizing A), 512^2 x 768 x 512, FP32 and binary16 plans."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_07226_gb300 import inputs, xct
+    wl = inputs.WORKLOADS[WORKLOAD]
+    n, m, nd = wl["n"], wl["m"], wl["nd"]
+    out = {"mode": "matfree", "n": n, "angles": m, "bins": nd}
+    with xct.Plan(n, m, nd, "f32", cos_sin=inputs.angle_table(m)) as p32, \
+            xct.Plan(n, m, nd, "f16", cos_sin=inputs.angle_table(m)) as p16:
+        nnz = p32.stats()["nnz"]
+        out["nnz"] = nnz
+        for S in (8, 64):
+            g = torch.Generator(device="cuda").manual_seed(0)
+            x = torch.rand((S, n, n), device="cuda", generator=g)
+            y = torch.empty((S, m, nd), device="cuda")
+
+            def timed(fn, reps):
+                fn()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    fn()
+                e1.record()
+                torch.cuda.synchronize()
+                return e0.elapsed_time(e1) / reps
+
+            t_mf = timed(lambda: xct.xct_project_matfree(p32.handle, x, y, S), max(1, args.steps // 3))
+            t32 = timed(lambda: p32.project(x, out=y), args.steps)
+            t16 = timed(lambda: p16.project(x, out=y), args.steps)
+            out[f"S{S}"] = {"matfree_ms": t_mf, "memoized_f32_ms": t32, "memoized_f16_ms": t16,
+                            "matfree_gflops": 2.0 * nnz * S / (t_mf * 1e-3) / 1e9,
+                            "speedup_memoized_f32": t_mf / t32, "speedup_memoized_f16": t_mf / t16}
+    print(json.dumps(out))
+
+
 def _large_slices(arg):
     s0, count = arg
     from paper_2009_07226_gb300 import inputs
@@ -691,7 +731,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="cgls", choices=["cgls", "products", "batch", "tv", "large", "cusparse"])
+    ap.add_argument("--mode", default="cgls", choices=["cgls", "products", "batch", "tv", "large", "cusparse", "matfree"])
     ap.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16"])
     args = ap.parse_args()
     if args.mode == "products":
@@ -704,6 +744,8 @@ def main():
         run_large(args)
     elif args.mode == "cusparse":
         run_cusparse(args)
+    elif args.mode == "matfree":
+        run_matfree(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -123,6 +123,17 @@ xct_status xct_project(xct_plan_t plan, const float* x, float* y, int32_t S,
 xct_status xct_backproject(xct_plan_t plan, const float* y, float* x,
                            int32_t S, void* stream);
 
+/*
+ * xct_project_matfree -- y = A x without the stored matrix: every ray is
+ * traced again on the GPU with the plan's geometry and arithmetic (the
+ * recomputation that memoizing A avoids, Sec. II-B) and RN32(length) * x is
+ * accumulated in FP32, 8 slices per trace.  A comparison point and the form
+ * for grids whose A does not fit in memory.  x, y: natural layouts, host or
+ * device.  Synchronous.
+ */
+xct_status xct_project_matfree(xct_plan_t plan, const float* x, float* y, int32_t S,
+                               void* stream);
+
 /* CGLS flags. */
 #define XCT_CGLS_X0 1u        /* start from the x passed in (else from 0) */
 #define XCT_CGLS_NO_GRAPH 2u  /* launch kernels directly, no CUDA graph */

@@ -590,6 +590,32 @@ xct_status xct_cgls(xct_plan_t plan, const float* y, float* x, int32_t S, int32_
   return cgls_impl(*plan, y, x, S, iters, flags, resid, nullptr, static_cast<cudaStream_t>(stream));
 }
 
+xct_status xct_project_matfree(xct_plan_t plan, const float* x, float* y, int32_t S, void* stream) {
+  XCT_TRY(check_plan(plan));
+  if (S < 0 || ((!x || !y) && S > 0)) {
+    set_error("bad arguments (S = %d)", S);
+    return XCT_ERR_INVALID;
+  }
+  if (S == 0) return XCT_OK;
+  Plan& p = *plan;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar(s);
+  DevView xv, yv;
+  XCT_TRY(device_view(x, (size_t)S * p.npix, true, ar, s, xv));
+  XCT_TRY(device_view(y, (size_t)S * p.nray, false, ar, s, yv));
+  double* cs_dev;
+  XCT_TRY(ar.get(&cs_dev, 2 * (size_t)p.g.n_angles));
+  XCT_TRY_CUDA(cudaMemcpyAsync(cs_dev, p.cs.data(), sizeof(double) * 2 * p.g.n_angles,
+                               cudaMemcpyHostToDevice, s));
+  XCT_TRY(matfree_project(p, cs_dev, xv.dev, yv.dev, S, s));
+  if (yv.host) {
+    XCT_TRY_CUDA(cudaMemcpyAsync(y, yv.dev, sizeof(float) * S * p.nray, cudaMemcpyDeviceToHost, s));
+  }
+  // the angle table copy comes from host memory owned by the plan: wait for it
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  return XCT_OK;
+}
+
 int64_t xct_cgls_state_bytes(xct_plan_t plan, int32_t S) {
   if (!plan || S < 1) return 0;
   return (int64_t)state_bytes(plan->npix, plan->nray, S);

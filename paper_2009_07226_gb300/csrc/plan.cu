@@ -316,6 +316,36 @@ __global__ void siddon_fill_kernel(GeomDev g, const int32_t* ray_inv, const int3
   if (setup_row(g, ray_inv[h], r)) trace(r, sink);
 }
 
+// Matrix-free projection (no stored A): each thread traces one ray with the
+// plan builder's arithmetic and accumulates RN32(length) * x[s][pixel] in
+// FP32 for kMfSlices slices per pass, retracing the ray for the next ones.
+constexpr int kMfSlices = 8;
+
+struct ProjSink {
+  const float* x;      // natural [S][npix]
+  int64_t npix;
+  int s0, ns;
+  float acc[kMfSlices];
+  __device__ void operator()(int pix, double len) {
+    const float l = (float)len;
+#pragma unroll
+    for (int k = 0; k < kMfSlices; ++k)
+      if (k < ns) acc[k] = fmaf(l, __ldg(x + (size_t)(s0 + k) * npix + pix), acc[k]);
+  }
+};
+
+__global__ void matfree_project_kernel(GeomDev g, const float* x, float* y, int S, int64_t nray) {
+  const int64_t ray = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (ray >= nray) return;
+  Ray r;
+  const bool hit = setup_row(g, (int32_t)ray, r);
+  for (int s0 = 0; s0 < S; s0 += kMfSlices) {
+    ProjSink sink{x, (int64_t)g.n * g.n, s0, min(kMfSlices, S - s0), {}};
+    if (hit) trace(r, sink);
+    for (int k = 0; k < sink.ns; ++k) y[(size_t)(s0 + k) * nray + ray] = sink.acc[k];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // 3. transpose
 // ---------------------------------------------------------------------------
@@ -926,6 +956,16 @@ xct_status time_product(const Layout& L, Plan& p, cudaStream_t s, double* ms_out
     return XCT_ERR_CUDA;
   }
   *ms_out = ms / 2.0;
+  return XCT_OK;
+}
+
+xct_status matfree_project(const Plan& p, const double* cs_dev, const float* x, float* y, int S,
+                           cudaStream_t s) {
+  const xct_geometry& g = p.g;
+  GeomDev gd{g.n, g.n_angles, g.n_det, g.det_spacing, g.det_offset, g.min_seg, cs_dev};
+  matfree_project_kernel<<<grid_for(p.nray, 128), 128, 0, s>>>(gd, x, y, S, p.nray);
+  count_launch();
+  XCT_TRY_CUDA(cudaGetLastError());
   return XCT_OK;
 }
 

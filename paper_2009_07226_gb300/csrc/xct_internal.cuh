@@ -168,6 +168,9 @@ struct Plan {
 
 // plan building (plan.cu)
 xct_status build_plan(Plan& p, cudaStream_t s);
+// y = A x without the stored matrix: every ray traced again (plan.cu)
+xct_status matfree_project(const Plan& p, const double* cs_dev, const float* x, float* y, int S,
+                           cudaStream_t s);
 xct_status export_matrix(Plan& p, int what, int64_t* rowptr, int32_t* col,
                          double* val, int64_t* nnz);
 

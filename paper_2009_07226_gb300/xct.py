@@ -101,6 +101,8 @@ _SIGNATURES = [
     ("xct_last_error", ctypes.c_char_p, []),
     ("xct_launch_count", ctypes.c_int64, []),
     ("xct_cgls_state_bytes", ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int32]),
+    ("xct_project_matfree", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.c_void_p]),
     ("xct_cgls_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
@@ -205,6 +207,10 @@ def xct_backproject(plan: int, y, x, S: int, stream=None) -> None:
 
 def xct_cgls(plan: int, y, x, S: int, iters: int, flags: int = 0, resid=None, stream=None) -> None:
     _check(lib().xct_cgls(plan, _ptr(y), _ptr(x), S, iters, flags, _ptr(resid), _stream(stream)))
+
+
+def xct_project_matfree(plan: int, x, y, S: int, stream=None) -> None:
+    _check(lib().xct_project_matfree(plan, _ptr(x), _ptr(y), S, _stream(stream)))
 
 
 def xct_cgls_state_bytes(plan: int, S: int) -> int:
