@@ -214,12 +214,14 @@ def run_ours(args):
 
     per_rank = inputs.WORKLOADS[WORKLOAD]["slices"]
     first, count = shard.weak_range(per_rank, rank)
-    w = inputs.make_workload(WORKLOAD, slices=count, slice_offset=first, with_images=False,
+    w = inputs.make_workload(WORKLOAD, slices=count, slice_offset=first, with_images=True,
                              volume_slices=per_rank * world)
     n, m, nd, S, K = w["n"], w["m"], w["nd"], w["slices"], w["iters"]
     y = torch.tensor(w["sino"], dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    plans = {k: xct.Plan(n, m, nd, k, cos_sin=w["cos_sin"]) for k in ("f16", "f32", "f16a")}
+    # the FP32 plan also keeps the FP64 matrices for the double-precision yardstick
+    plans = {k: xct.Plan(n, m, nd, k, cos_sin=w["cos_sin"], keep_f64=(k == "f32"))
+             for k in ("f16", "f32", "f16a")}
     nnz = plans["f16"].stats()["nnz"]
     flops_step = (2 * K + 1) * 2.0 * nnz * S
     xs = {k: torch.empty((S, n, n), dtype=torch.float32, device=dev) for k in plans}
@@ -308,6 +310,40 @@ def run_ours(args):
     proj_err = float(torch.linalg.norm((q16 - q32).double()) / torch.linalg.norm(q32.double()))
     track_max, track_final = float(track.max()), float(track[-1].max())
 
+    # double-precision yardstick (Sec. V compares double, single and 16-bit
+    # forms): one FP64 solve on the unrounded sinogram, one FP64 projection;
+    # every form's iterate and residual curve against it
+    p64 = plans["f32"]
+    y64 = torch.tensor(w["sino"], dtype=torch.float64, device=dev)
+    p64.project_f64(xs["f32"].double())                # warm-up of the FP64 kernels
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    barrier()
+    ev[0].record(stream)
+    x64p = p64.project_f64(xs["f32"].double(), stream=stream)
+    ev[1].record(stream)
+    log64 = torch.zeros((K + 1, S, 2), dtype=torch.float64, device=dev)
+    x64 = torch.empty((S, n, n), dtype=torch.float64, device=dev)
+    xct.xct_cgls_f64(p64.handle, y64, x64, S, K, 0, log64, stream)
+    ev[2].record(stream)
+    barrier()
+    proj64_ms, ms64 = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    proj_err64 = {k: float(torch.linalg.norm(q.double() - x64p) / torch.linalg.norm(x64p))
+                  for k, q in (("f16", q16), ("f32", q32))}
+    phantom = torch.tensor(w["images"], dtype=torch.float64, device=dev)
+
+    def err_vs_phantom(x):
+        return float(torch.linalg.norm(x.double() - phantom) / torch.linalg.norm(phantom))
+
+    vs64 = {"phantom_rel_err": {"f64": err_vs_phantom(x64)}}
+    for kind in plans:
+        vs64["phantom_rel_err"][kind] = err_vs_phantom(xs[kind])
+    for kind in plans:
+        dev_k = (logs[kind] / log64[:, :, 0] - 1.0).abs()
+        vs64[kind] = {"rel_err": float(torch.linalg.norm(xs[kind].double() - x64) / torch.linalg.norm(x64)),
+                      "residual_curve_max_rel_dev": float(dev_k.max()),
+                      "residual_curve_final_rel_dev": float(dev_k[-1].max())}
+    del x64p
+
     if rank != 0:
         return
     st16 = plans["f16"].stats()
@@ -358,6 +394,14 @@ def run_ours(args):
                                                           "final_rel_dev": float(track_a[-1].max())},
                                "rel_err_vs_fp32": rel_a},
         "rel_err_projection_mixed_vs_fp32": proj_err,
+        "fp64": {"ms_per_step": ms64, "value": flops_step / (ms64 * 1e-3) / 1e9, "unit": "GFLOP/s",
+                 "project_ms": proj64_ms,
+                 "project_tflops": 2.0 * nnz * S / (proj64_ms * 1e-3) / 1e12,
+                 "project_frac_of_fp64_nominal": 2.0 * nnz * S / (proj64_ms * 1e-3) / 1e12 / 1.25,
+                 "note": "one solve, kept FP64 CSR, FP64 FMAs (nominal GB300 FP64 rate 1.25 TFLOP/s); "
+                         "FP32 and binary16 forms use the FP32-rounded sinogram"},
+        "vs_fp64": vs64,
+        "rel_err_projection_vs_fp64": proj_err64,
         "graph_ms_per_step": graph_ms,
         "other_f16_ms_per_step": timed.parts["f16"],
         "kernel_ms": {"project_f16": proj16, "backproject_f16": back16, "other_f16_per_step": other16,

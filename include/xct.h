@@ -134,6 +134,23 @@ xct_status xct_backproject(xct_plan_t plan, const float* y, float* x,
 xct_status xct_project_matfree(xct_plan_t plan, const float* x, float* y, int32_t S,
                                void* stream);
 
+/*
+ * xct_project_f64 / xct_backproject_f64 / xct_cgls_f64 -- the double-precision
+ * form that Sec. V measures the single, half and mixed forms against: the
+ * plan's kept FP64 matrix values (the plan must be built with
+ * XCT_PLAN_KEEP_F64, else XCT_ERR_INVALID), float64 vectors, FP64 FMAs and
+ * FP64 CGLS scalars.  x: [S][n][n] float64, y: [S][n_angles][n_det] float64
+ * (natural layouts as above), host or device.  xct_cgls_f64 runs the
+ * recurrence of xct_cgls (flags: XCT_CGLS_X0 only; resid as there; the same
+ * stop and XCT_ERR_BREAKDOWN rules) with launches issued directly (no
+ * graph), and returns when the solve is done.  The products are bound by
+ * the GPU's FP64 FMA rate.
+ */
+xct_status xct_project_f64(xct_plan_t plan, const double* x, double* y, int32_t S,
+                           void* stream);
+xct_status xct_backproject_f64(xct_plan_t plan, const double* y, double* x, int32_t S,
+                               void* stream);
+
 /* CGLS flags. */
 #define XCT_CGLS_X0 1u        /* start from the x passed in (else from 0) */
 #define XCT_CGLS_NO_GRAPH 2u  /* launch kernels directly, no CUDA graph */
@@ -156,6 +173,8 @@ xct_status xct_project_matfree(xct_plan_t plan, const float* x, float* y, int32_
  */
 xct_status xct_cgls(xct_plan_t plan, const float* y, float* x, int32_t S,
                     int32_t iters, uint32_t flags, double* resid, void* stream);
+xct_status xct_cgls_f64(xct_plan_t plan, const double* y, double* x, int32_t S,
+                        int32_t iters, uint32_t flags, double* resid, void* stream);
 
 /* CGLS state flags (xct_cgls_state). */
 #define XCT_CGLS_SAVE 32u    /* write the state after the last iteration */

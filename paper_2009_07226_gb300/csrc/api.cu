@@ -84,21 +84,24 @@ bool is_host_pointer(const void* p) {
 }
 
 // A vector argument that may live on the host: a device view of it.
-struct DevView {
-  float* dev = nullptr;
+template <class T>
+struct DevViewT {
+  T* dev = nullptr;
   bool host = false;
 };
+using DevView = DevViewT<float>;
 
-xct_status device_view(const float* user, size_t count, bool copy_in, Arena& ar, cudaStream_t s,
-                       DevView& v) {
+template <class T>
+xct_status device_view(const T* user, size_t count, bool copy_in, Arena& ar, cudaStream_t s,
+                       DevViewT<T>& v) {
   v.host = is_host_pointer(user);
   if (!v.host) {
-    v.dev = const_cast<float*>(user);
+    v.dev = const_cast<T*>(user);
     return XCT_OK;
   }
   XCT_TRY(ar.get(&v.dev, count));
   if (copy_in && count)
-    XCT_TRY_CUDA(cudaMemcpyAsync(v.dev, user, count * sizeof(float), cudaMemcpyHostToDevice, s));
+    XCT_TRY_CUDA(cudaMemcpyAsync(v.dev, user, count * sizeof(T), cudaMemcpyHostToDevice, s));
   return XCT_OK;
 }
 
@@ -613,6 +616,83 @@ xct_status xct_project_matfree(xct_plan_t plan, const float* x, float* y, int32_
   }
   // the angle table copy comes from host memory owned by the plan: wait for it
   XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  return XCT_OK;
+}
+
+static xct_status apply_f64(xct_plan_t plan, bool transposed, const double* in, double* out, int32_t S,
+                     void* stream) {
+  XCT_TRY(check_plan(plan));
+  if (S < 0 || ((!in || !out) && S > 0)) {
+    set_error("bad arguments (S = %d)", S);
+    return XCT_ERR_INVALID;
+  }
+  Plan& p = *plan;
+  if (!p.a_val) {
+    set_error("the FP64 path needs a plan built with XCT_PLAN_KEEP_F64");
+    return XCT_ERR_INVALID;
+  }
+  if (S == 0) return XCT_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t nin = transposed ? p.nray : p.npix, nout = transposed ? p.npix : p.nray;
+  Arena ar(s);
+  DevViewT<double> iv, ov;
+  XCT_TRY(device_view(in, (size_t)S * nin, true, ar, s, iv));
+  XCT_TRY(device_view(out, (size_t)S * nout, false, ar, s, ov));
+  XCT_TRY(f64_apply(p, transposed, iv.dev, ov.dev, S, s));
+  if (ov.host) {
+    XCT_TRY_CUDA(cudaMemcpyAsync(out, ov.dev, sizeof(double) * S * nout, cudaMemcpyDeviceToHost, s));
+    XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  }
+  return XCT_OK;
+}
+
+xct_status xct_project_f64(xct_plan_t plan, const double* x, double* y, int32_t S, void* stream) {
+  return apply_f64(plan, false, x, y, S, stream);
+}
+
+xct_status xct_backproject_f64(xct_plan_t plan, const double* y, double* x, int32_t S,
+                               void* stream) {
+  return apply_f64(plan, true, y, x, S, stream);
+}
+
+xct_status xct_cgls_f64(xct_plan_t plan, const double* y, double* x, int32_t S, int32_t iters,
+                        uint32_t flags, double* resid, void* stream) {
+  XCT_TRY(check_plan(plan));
+  if (S < 0 || iters < 0 || ((!x || !y) && S > 0)) {
+    set_error("bad arguments (S = %d, iters = %d)", S, iters);
+    return XCT_ERR_INVALID;
+  }
+  if (flags & ~XCT_CGLS_X0) {
+    set_error("unknown FP64 CGLS flags 0x%x", flags);
+    return XCT_ERR_INVALID;
+  }
+  Plan& p = *plan;
+  if (!p.a_val) {
+    set_error("the FP64 path needs a plan built with XCT_PLAN_KEEP_F64");
+    return XCT_ERR_INVALID;
+  }
+  if (S == 0) return XCT_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool x0 = (flags & XCT_CGLS_X0) != 0;
+  Arena ar(s);
+  DevViewT<double> yv, xv;
+  XCT_TRY(device_view(y, (size_t)S * p.nray, true, ar, s, yv));
+  XCT_TRY(device_view(x, (size_t)S * p.npix, x0, ar, s, xv));
+  double* log = nullptr;
+  if (resid) XCT_TRY(ar.get(&log, (size_t)(iters + 1) * S * 2));
+  int any = 0;
+  XCT_TRY(f64_cgls(p, yv.dev, xv.dev, S, iters, x0, log, &any, s));
+  if (resid)
+    XCT_TRY_CUDA(cudaMemcpyAsync(resid, log, sizeof(double) * (iters + 1) * S * 2,
+                                 is_host_pointer(resid) ? cudaMemcpyDeviceToHost
+                                                        : cudaMemcpyDeviceToDevice, s));
+  if (xv.host)
+    XCT_TRY_CUDA(cudaMemcpyAsync(x, xv.dev, sizeof(double) * S * p.npix, cudaMemcpyDeviceToHost, s));
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  if (!any) {
+    set_error("CGLS breakdown: every slice has A^T r_0 = 0");
+    return XCT_ERR_BREAKDOWN;
+  }
   return XCT_OK;
 }
 

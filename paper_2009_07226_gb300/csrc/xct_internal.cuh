@@ -171,6 +171,13 @@ xct_status build_plan(Plan& p, cudaStream_t s);
 // y = A x without the stored matrix: every ray traced again (plan.cu)
 xct_status matfree_project(const Plan& p, const double* cs_dev, const float* x, float* y, int S,
                            cudaStream_t s);
+// the double-precision form (f64.cu): products and CGLS on the kept FP64
+// matrices, natural-layout device vectors; f64_cgls writes log [iters+1][S][2]
+// (device, nullable) and whether any slice was active after the start
+xct_status f64_apply(Plan& p, bool transposed, const double* in, double* out, int S,
+                     cudaStream_t s);
+xct_status f64_cgls(Plan& p, const double* y, double* x, int S, int iters, bool x0, double* log,
+                    int* any_active, cudaStream_t s);
 xct_status export_matrix(Plan& p, int what, int64_t* rowptr, int32_t* col,
                          double* val, int64_t* nnz);
 

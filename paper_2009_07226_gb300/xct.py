@@ -106,6 +106,13 @@ _SIGNATURES = [
     ("xct_cgls_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
+    ("xct_project_f64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                       ctypes.c_int32, ctypes.c_void_p]),
+    ("xct_backproject_f64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.c_void_p]),
+    ("xct_cgls_f64", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
+                                    ctypes.c_void_p, ctypes.c_void_p]),
     ("xct_set_wait_limit", ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     ("xct_plan_check", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("xct_version", ctypes.c_char_p, []),
@@ -211,6 +218,20 @@ def xct_cgls(plan: int, y, x, S: int, iters: int, flags: int = 0, resid=None, st
 
 def xct_project_matfree(plan: int, x, y, S: int, stream=None) -> None:
     _check(lib().xct_project_matfree(plan, _ptr(x), _ptr(y), S, _stream(stream)))
+
+
+def xct_project_f64(plan: int, x, y, S: int, stream=None) -> None:
+    _check(lib().xct_project_f64(plan, _ptr(x), _ptr(y), S, _stream(stream)))
+
+
+def xct_backproject_f64(plan: int, y, x, S: int, stream=None) -> None:
+    _check(lib().xct_backproject_f64(plan, _ptr(y), _ptr(x), S, _stream(stream)))
+
+
+def xct_cgls_f64(plan: int, y, x, S: int, iters: int, flags: int = 0, resid=None,
+                 stream=None) -> None:
+    _check(lib().xct_cgls_f64(plan, _ptr(y), _ptr(x), S, iters, flags, _ptr(resid),
+                              _stream(stream)))
 
 
 def xct_cgls_state_bytes(plan: int, S: int) -> int:
@@ -408,6 +429,38 @@ class Plan:
                                                     device=y.device)
         xct_backproject(self.handle, y, x, S, stream)
         return x
+
+    def project_f64(self, x, out=None, stream=None):
+        """y = A x in FP64 (plan built with keep_f64); x [S, n, n] float64."""
+        import torch
+        S = x.shape[0]
+        y = out if out is not None else torch.empty((S, self.m, self.nd), dtype=torch.float64,
+                                                    device=x.device)
+        xct_project_f64(self.handle, x, y, S, stream)
+        return y
+
+    def backproject_f64(self, y, out=None, stream=None):
+        """x = A^T y in FP64 (plan built with keep_f64); y [S, M, N_d] float64."""
+        import torch
+        S = y.shape[0]
+        x = out if out is not None else torch.empty((S, self.n, self.n), dtype=torch.float64,
+                                                    device=y.device)
+        xct_backproject_f64(self.handle, y, x, S, stream)
+        return x
+
+    def cgls_f64(self, y, iters: int, x0=None, resid: bool = False, stream=None):
+        """FP64 CGLS (plan built with keep_f64); y [S, M, N_d] float64."""
+        import torch
+        S = y.shape[0]
+        flags = 0
+        if x0 is not None:
+            x = x0.clone()
+            flags |= XCT_CGLS_X0
+        else:
+            x = torch.empty((S, self.n, self.n), dtype=torch.float64, device=y.device)
+        log = torch.zeros((iters + 1, S, 2), dtype=torch.float64, device=y.device) if resid else None
+        xct_cgls_f64(self.handle, y, x, S, iters, flags, log, stream)
+        return (x, log) if resid else x
 
     def cgls(self, y, iters: int, x0=None, resid: bool = False, flags: int = 0, stream=None):
         """CGLS from x0 (or 0); returns x [S, n, n] (and the residual log

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     with open(os.path.join(ROOT, "include", "xct.h")) as f:
         text = f.read()
-    return sorted(set(re.findall(r"\b(xct_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(xct_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
