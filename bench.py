@@ -475,6 +475,59 @@ def run_products(args):
                       "backproject_gflops": 2.0 * nnz * S / tb / 1e6}))
 
 
+def run_pipeline(args):
+    """Products with pinned host vectors over several slice tiles (256
+    slices of the workload's geometry): the library's slice-tile pipeline
+    (copies on a second stream overlapping the tiles' products) against the
+    same work done serially (copy in, product, copy out) and against the
+    device-resident product alone."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2009_07226_gb300 import inputs, xct
+    wl = inputs.WORKLOADS[WORKLOAD]
+    n, m, nd, S = wl["n"], wl["m"], wl["nd"], 4 * wl["slices"]
+    plan = xct.Plan(n, m, nd, args.storage, cos_sin=inputs.angle_table(m))
+    nnz = plan.stats()["nnz"]
+    g = torch.Generator(device="cuda").manual_seed(0)
+    xd = torch.rand((S, n, n), device="cuda", generator=g)
+    yd = torch.empty((S, m, nd), device="cuda")
+    xh, yh = xd.cpu().pin_memory(), torch.empty((S, m, nd)).pin_memory()
+    xd2 = torch.empty_like(xd)
+    stream = torch.cuda.current_stream()
+
+    def device_only():
+        xct.xct_project(plan.handle, xd, yd, S, stream)
+
+    def serial():
+        xd2.copy_(xh, non_blocking=True)
+        xct.xct_project(plan.handle, xd2, yd, S, stream)
+        yh.copy_(yd, non_blocking=True)
+
+    def pipelined():
+        xct.xct_project(plan.handle, xh, yh, S, stream)
+
+    res = {}
+    for name, fn in (("device", device_only), ("serial", serial), ("pipelined", pipelined)):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            fn()
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) / args.steps * 1e3
+        res[name] = {"ms": ms, "gflops": 2.0 * nnz * S / (ms * 1e-3) / 1e9}
+    ref = yd.cpu()
+    pipelined()
+    same = bool(torch.equal(yh, ref))
+    print(json.dumps({"mode": "pipeline", "storage": args.storage, "slices": S, "nnz": nnz,
+                      "h2d_bytes": S * n * n * 4, "d2h_bytes": S * m * nd * 4,
+                      "pipelined_equals_device": same, **res,
+                      "pipelined_speedup_vs_serial": res["serial"]["ms"] / res["pipelined"]["ms"]}))
+
+
 def _job_sinos(jobs):
     """Sinograms of the uneven batch, generated on the host cores (spawned
     workers, before any GPU work)."""
@@ -775,8 +828,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="cgls", choices=["cgls", "products", "batch", "tv", "large", "cusparse", "matfree"])
-    ap.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16"])
+    ap.add_argument("--mode", default="cgls", choices=["cgls", "products", "batch", "tv", "large", "cusparse", "matfree",
+                             "pipeline"])
+    ap.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16", "f16a", "bf16a"])
     args = ap.parse_args()
     if args.mode == "products":
         run_products(args)
@@ -790,6 +844,8 @@ def main():
         run_cusparse(args)
     elif args.mode == "matfree":
         run_matfree(args)
+    elif args.mode == "pipeline":
+        run_pipeline(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

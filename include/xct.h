@@ -17,7 +17,11 @@
  *   - Vector arguments (images x, sinograms y) may be device pointers or host
  *     pointers (pageable or pinned); the library detects which.  Host
  *     arguments are copied in and out inside the call, which then
- *     synchronises `stream` before returning.
+ *     synchronises `stream` before returning.  xct_project and
+ *     xct_backproject with host vectors and more slices than one slice tile
+ *     pipeline the copies per tile on two internal copy streams (one per
+ *     direction) so they overlap the other tiles' products; pinned host
+ *     memory lets them run concurrently.
  *   - The caller owns every x / y buffer.  A plan owns its matrices; they are
  *     released by xct_free().
  *   - Image layout: x[s][iy][ix], S slices of n*n float32, slice-major,

@@ -429,6 +429,106 @@ xct_status cgls_impl(Plan& p, const float* y, float* x, int32_t S, int32_t iters
   return XCT_OK;
 }
 
+// The product kernel's bounded waits report through the plan's error flag.
+xct_status check_kernel_flag(Plan& p, cudaStream_t s) {
+  int kerr = 0;
+  XCT_TRY_CUDA(cudaMemcpyAsync(&kerr, p.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  if (kerr) {
+    XCT_TRY_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), s));
+    set_error("a bounded wait in the product kernel ran out; results are invalid");
+    return XCT_ERR_TIMEOUT;
+  }
+  return XCT_OK;
+}
+
+// A copy stream that is drained before it is destroyed (declared after the
+// arena whose buffers its copies use, so it goes first).
+struct CopyStream {
+  cudaStream_t s = nullptr;
+  ~CopyStream() {
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  }
+};
+
+// Host vectors and several slice tiles: the slice-tile pipeline.  Tile t+1's
+// host-to-device copy and tile t-1's device-to-host copy run on two copy
+// streams (one per direction, so neither waits behind the other) while tile
+// t is packed, multiplied and unpacked on `s`, with two device buffers per
+// vector (the single-GPU form of the paper's pipelined
+// minibatches, whose transfers overlap the products, Sec. III-D).  Each
+// tile is computed exactly as in the one-launch form, so the results are
+// identical.
+xct_status apply_pipelined(Plan& p, bool transposed, const float* in, float* out, int32_t S,
+                           int st, int ntiles, bool in_host, bool out_host, cudaStream_t s) {
+  const Layout& L = transposed ? p.lat : p.la;
+  const int32_t* in_inv = transposed ? p.ray_inv : p.pix_inv;
+  const int32_t* out_inv = transposed ? p.pix_inv : p.ray_inv;
+  const int64_t nin = L.ncols, nout = L.nrows;
+  Arena ar(s);
+  float *Xn[2] = {nullptr, nullptr}, *Yn[2] = {nullptr, nullptr}, *Xi[2], *Yi[2];
+  uint32_t* mx[2];
+  uint16_t* h16[2] = {nullptr, nullptr};
+  int* work;
+  for (int b = 0; b < 2; ++b) {
+    if (in_host) XCT_TRY(ar.get(&Xn[b], (size_t)nin * st));
+    if (out_host) XCT_TRY(ar.get(&Yn[b], (size_t)nout * st));
+    XCT_TRY(ar.get(&Xi[b], (size_t)nin * st));
+    XCT_TRY(ar.get(&Yi[b], (size_t)nout * st));
+    XCT_TRY(ar.get(&mx[b], (size_t)st));
+    if (stages16(p.storage)) XCT_TRY(ar.get(&h16[b], (size_t)nin * st));
+  }
+  XCT_TRY(ar.get(&work, 1));
+  CopyStream cin, cout;
+  XCT_TRY_CUDA(cudaStreamCreateWithFlags(&cin.s, cudaStreamNonBlocking));
+  XCT_TRY_CUDA(cudaStreamCreateWithFlags(&cout.s, cudaStreamNonBlocking));
+  EventGuard ev_alloc, ev_in[2], ev_used[2], ev_out[2], ev_d2h[2];
+  for (EventGuard* e : {&ev_alloc, &ev_in[0], &ev_in[1], &ev_used[0], &ev_used[1], &ev_out[0],
+                        &ev_out[1], &ev_d2h[0], &ev_d2h[1]})
+    XCT_TRY_CUDA(cudaEventCreateWithFlags(&e->e, cudaEventDisableTiming));
+  // the buffers are stream-ordered allocations on s
+  XCT_TRY_CUDA(cudaEventRecord(ev_alloc.e, s));
+  XCT_TRY_CUDA(cudaStreamWaitEvent(cin.s, ev_alloc.e, 0));
+  XCT_TRY_CUDA(cudaStreamWaitEvent(cout.s, ev_alloc.e, 0));
+  for (int t = 0; t < ntiles; ++t) {
+    const int b = t & 1;
+    const int St = S - t * st < st ? S - t * st : st;
+    const float* xin = in + (size_t)t * st * nin;
+    if (in_host) {
+      if (t >= 2) XCT_TRY_CUDA(cudaStreamWaitEvent(cin.s, ev_used[b].e, 0));
+      XCT_TRY_CUDA(cudaMemcpyAsync(Xn[b], xin, sizeof(float) * St * nin, cudaMemcpyHostToDevice,
+                                   cin.s));
+      XCT_TRY_CUDA(cudaEventRecord(ev_in[b].e, cin.s));
+      XCT_TRY_CUDA(cudaStreamWaitEvent(s, ev_in[b].e, 0));
+      xin = Xn[b];
+    }
+    XCT_TRY_CUDA(cudaMemsetAsync(mx[b], 0, sizeof(uint32_t) * st, s));
+    XCT_TRY(to_internal(xin, Xi[b], in_inv, nin, St, st, 1, mx[b], s));
+    if (in_host) XCT_TRY_CUDA(cudaEventRecord(ev_used[b].e, s));
+    SpmmArgs a{&L, Xi[b], Yi[b], st, 1, p.storage, p.mat_scale_exp, mx[b], nullptr, h16[b], work,
+               p.err};
+    XCT_TRY(spmm(a, s));
+    float* yout = out + (size_t)t * st * nout;
+    if (out_host) {
+      if (t >= 2) XCT_TRY_CUDA(cudaStreamWaitEvent(s, ev_d2h[b].e, 0));
+      XCT_TRY(to_natural(Yi[b], Yn[b], out_inv, nout, St, st, 1, s));
+      XCT_TRY_CUDA(cudaEventRecord(ev_out[b].e, s));
+      XCT_TRY_CUDA(cudaStreamWaitEvent(cout.s, ev_out[b].e, 0));
+      XCT_TRY_CUDA(cudaMemcpyAsync(yout, Yn[b], sizeof(float) * St * nout, cudaMemcpyDeviceToHost,
+                                   cout.s));
+      XCT_TRY_CUDA(cudaEventRecord(ev_d2h[b].e, cout.s));
+    } else {
+      XCT_TRY(to_natural(Yi[b], yout, out_inv, nout, St, st, 1, s));
+    }
+  }
+  XCT_TRY_CUDA(cudaStreamSynchronize(cin.s));
+  XCT_TRY_CUDA(cudaStreamSynchronize(cout.s));
+  return check_kernel_flag(p, s);
+}
+
 xct_status apply_impl(Plan& p, bool transposed, const float* in, float* out, int32_t S,
                       cudaStream_t s) {
   const Layout& L = transposed ? p.lat : p.la;
@@ -438,6 +538,9 @@ xct_status apply_impl(Plan& p, bool transposed, const float* in, float* out, int
   const int st = pick_slices_per_tile(p.storage, S);
   const int ntiles = (S + st - 1) / st;
   const int S_pad = st * ntiles;
+  const bool in_host = is_host_pointer(in), out_host = is_host_pointer(out);
+  if ((in_host || out_host) && ntiles > 1)
+    return apply_pipelined(p, transposed, in, out, S, st, ntiles, in_host, out_host, s);
   Arena ar(s);
   DevView iv, ov;
   XCT_TRY(device_view(in, (size_t)S * nin, true, ar, s, iv));
@@ -458,14 +561,7 @@ xct_status apply_impl(Plan& p, bool transposed, const float* in, float* out, int
   XCT_TRY(to_natural(Yi, ov.dev, out_inv, nout, S, st, ntiles, s));
   if (ov.host) {
     XCT_TRY_CUDA(cudaMemcpyAsync(out, ov.dev, sizeof(float) * S * nout, cudaMemcpyDeviceToHost, s));
-    int kerr = 0;
-    XCT_TRY_CUDA(cudaMemcpyAsync(&kerr, p.err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    XCT_TRY_CUDA(cudaStreamSynchronize(s));
-    if (kerr) {
-      XCT_TRY_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), s));
-      set_error("a bounded wait in the product kernel ran out; results are invalid");
-      return XCT_ERR_TIMEOUT;
-    }
+    return check_kernel_flag(p, s);
   }
   return XCT_OK;
 }
