@@ -342,6 +342,19 @@ def run_ours(args):
         vs64[kind] = {"rel_err": float(torch.linalg.norm(xs[kind].double() - x64) / torch.linalg.norm(x64)),
                       "residual_curve_max_rel_dev": float(dev_k.max()),
                       "residual_curve_final_rel_dev": float(dev_k[-1].max())}
+    # the same against FP64 after fewer iterations: where the iterates
+    # still agree (rounding differences grow once CGLS loses conjugacy)
+    vs64["rel_err_by_iteration"] = {"f16": {}, "f32": {}}
+    for k in (5, 10, 20):
+        x64k = torch.empty((S, n, n), dtype=torch.float64, device=dev)
+        xct.xct_cgls_f64(p64.handle, y64, x64k, S, k, 0, None, stream)
+        for kind in ("f16", "f32"):
+            xk = torch.empty((S, n, n), dtype=torch.float32, device=dev)
+            xct.xct_cgls(plans[kind].handle, y, xk, S, k, 0, None, stream)
+            vs64["rel_err_by_iteration"][kind][k] = float(torch.linalg.norm(xk.double() - x64k) /
+                                                          torch.linalg.norm(x64k))
+    vs64["rel_err_by_iteration"]["f16"][K] = vs64["f16"]["rel_err"]
+    vs64["rel_err_by_iteration"]["f32"][K] = vs64["f32"]["rel_err"]
     del x64p
 
     if rank != 0:
