@@ -6,9 +6,12 @@
 // each stage of each block into one of two shared-memory buffers with bulk
 // asynchronous copies (cp.async.bulk) counted in bytes on the buffer's
 // mbarrier: one copy per contiguous run of the stage's staged input rows
-// (runs of consecutive Hilbert ids, about 11 rows on average; the run list
-// itself arrives one stage ahead by another bulk copy), one for the stage's
-// packed entries and one for its segment headers.  The consumer warps (16
+// (runs of consecutive Hilbert ids, with gaps of a few unreferenced rows
+// filled in by the plan so that runs are longer; the run list itself
+// arrives one stage ahead by another bulk copy) and one for the stage's
+// packed entries.  Each copy costs the TMA unit a fixed time whatever its
+// size, so the segment headers (256 B) go through the producer's registers
+// instead.  The consumer warps (16
 // for 128-byte staged rows, 8 for 64-byte, 4 for 32-byte; 2, 3 or 4 CTAs per
 // SM) compute from shared memory only and release the buffer through a
 // second mbarrier; while they work on one stage the next one (possibly of the
@@ -279,11 +282,13 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
       int64_t r0, e0;
       int nr, np;
       uint32_t eb;
+      uint2 seg;   // this lane's 8 bytes of the stage's 16 segment headers
     };
     auto meta = [&](Ref& r) {
       r.r0 = 0; r.e0 = 0; r.nr = 0; r.np = 0; r.eb = 0;
       if (r.w >= 0 && r.s >= 0) {
         const PipeLayout& P = a.L[r.l];
+        r.seg = reinterpret_cast<const uint2*>(P.seg + r.s * kQuads)[lane];
         r.r0 = P.stage_run[r.s];
         r.nr = (int)(P.stage_run[r.s + 1] - r.r0);
         r.np = P.runs[r.r0 + r.nr - 1].y;   // the closing pair holds the row count
@@ -359,10 +364,14 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
       }
       if (real) {
         // one bulk copy per contiguous run of staged rows, plus the stage's
-        // packed entries and segment headers, all counted in bytes on the
-        // full barrier (the expected count is set before any copy starts)
-        if (lane == 0)
-          mbar_expect_tx(&full[buf], (uint32_t)np * C::PIXB + eb + 256u);
+        // packed entries, all counted in bytes on the full barrier (the
+        // expected count is set before any copy starts)
+        if (lane == 0) mbar_expect_tx(&full[buf], (uint32_t)np * C::PIXB + eb);
+        // the segment headers, loaded into the lanes' registers when the
+        // stage reference was made, go in by plain stores (the full
+        // barrier's arrival below publishes them with the header): one TMA
+        // request less per stage
+        reinterpret_cast<uint2*>(sbuf(buf))[lane] = cur.seg;
         __syncwarp();
         const int2* rl = plist(buf);
         unsigned char* xd = xbuf(buf);
@@ -374,10 +383,7 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
                      &full[buf]);
           }
         }
-        if (lane == 0) {
-          if (eb) bulk_g2s(ebuf(buf), P.ent + (size_t)cur.e0 * C::EB, eb, &full[buf]);
-          bulk_g2s(sbuf(buf), P.seg + cur.s * kQuads, 256u, &full[buf]);
-        }
+        if (lane == 0 && eb) bulk_g2s(ebuf(buf), P.ent + (size_t)cur.e0 * C::EB, eb, &full[buf]);
       }
       // the single arrival of this phase; it also publishes the header
       __syncwarp();
