@@ -522,7 +522,7 @@ __device__ void block_col_range(const CsrView& m, int64_t e0, int64_t e1, int32_
 // of up to 4 columns add 7.5% staged rows (A) and cut the runs of a stage
 // from 24 to 11; the binary16 products ran 5% / 3.5% faster, FP32 products
 // (twice the bytes per staged row) best with gaps of up to 2.
-inline int gap_fill_for(xct_dtype storage) { return storage == XCT_F32 ? 2 : 4; }
+inline int gap_fill_for(xct_dtype storage) { return storage == XCT_F32 ? 2 : 4; }   // < 32
 
 // Mark the block's columns of window [w0, w0 + kWinBits) in the bitmap (and
 // the gaps of at most `gap` columns between them inside the window).
@@ -544,6 +544,12 @@ __device__ void mark_window(const CsrView& m, int64_t e0, int64_t e1, int64_t w0
       const uint64_t lo = i > 0 ? bm[i - 1] : 0u, hi = i + 1 < kWinWords ? bm[i + 1] : 0u;
       const uint32_t mid = bm[i];
       uint32_t f = 0;
+      // an empty word lies inside a gap of at least 32 > `gap` columns, and a
+      // full word has nothing to fill
+      if (mid == 0u || mid == 0xffffffffu) {
+        fill[k] = 0u;
+        continue;
+      }
       for (int j = 0; j < 32; ++j) {
         if ((mid >> j) & 1u) continue;
         // nearest set bits below and above bit j of mid in the 96-bit view
