@@ -52,7 +52,7 @@ typedef enum {
   XCT_ERR_CUDA = 3,         /* a CUDA runtime call failed */
   XCT_ERR_TIMEOUT = 4,      /* a bounded device wait ran out */
   XCT_ERR_BREAKDOWN = 5,    /* CGLS: every slice stopped at k = 0 (zero data) */
-  XCT_ERR_UNSUPPORTED = 6   /* valid request outside what this build handles */
+  XCT_ERR_UNSUPPORTED = 6   /* valid request the library does not handle */
 } xct_status;
 
 /* Storage precision of a plan (Sec. III-C).  XCT_F32: values and staged

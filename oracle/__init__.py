@@ -27,7 +27,8 @@ What it computes, each step following the paper:
   semantics (Sec. III-C): 16-bit storage of matrix and input vectors with a
   power-of-two normalisation, products summed wide, output de-normalised.
 * ``tv_value_grad``   -- a smoothed isotropic total variation R(x) for Eq. 1
-  (the paper leaves R unspecified; this reading is listed in the design doc).
+  (the paper leaves R unspecified: sum of sqrt(dx^2 + dy^2 + eps^2) with
+  forward differences, 0 past the last row / column).
 """
 from __future__ import annotations
 
@@ -85,7 +86,9 @@ def _load():
 
 
 # --------------------------------------------------------------------------
-# Geometry (Sec. II-A; conventions fixed in the design doc)
+# Geometry (Sec. II-A gives no conventions: unit pixels centred on the
+# origin, ray (k, j) at offset t_j along the normal (cos, sin) of theta_k,
+# traversed along (-sin, cos))
 # --------------------------------------------------------------------------
 
 def default_angles(m: int) -> np.ndarray:
