@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -186,6 +187,7 @@ def run_reference(args):
 def cpu_baseline(w):
     """The oracle, as it stands, on this host's cores: one slice, a few
     iterations (a bounded sample of the same workload)."""
+    import oracle
     a, at = _oracle_setup(w)
     b = w["sino"][:1].reshape(1, -1)
     iters = 2
@@ -193,9 +195,41 @@ def cpu_baseline(w):
     t0 = time.perf_counter()
     _oracle_step(a, at, b, iters)
     dt = time.perf_counter() - t0
-    gf = (2 * iters + 1) * 2.0 * a.nnz / dt / 1e9
-    return {"value": gf, "unit": "GFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"1 of 64 slices, {iters} CGLS iterations, FP64 CSR products (OpenMP)"}
+    nprod = 2 * iters + 1
+    gf = nprod * 2.0 * a.nnz / dt / 1e9
+    # the same on one core (one iteration: 3 products)
+    prev = oracle.set_threads(1)
+    t1 = time.perf_counter()
+    _oracle_step(a, at, b, 1)
+    dt1 = time.perf_counter() - t1
+    oracle.set_threads(prev)
+    return {"value": gf, "unit": "GFLOP/s", "cores": prev, "kind": "oracle",
+            "sample": f"1 of 64 slices, {iters} CGLS iterations, FP64 CSR products (OpenMP)",
+            "ms_per_product": dt / nprod * 1e3, "ms_per_iteration": dt / iters * 1e3,
+            "single_core": {"value": 3 * 2.0 * a.nnz / dt1 / 1e9, "unit": "GFLOP/s",
+                            "ms_per_product": dt1 / 3 * 1e3},
+            "cpu": _cpu_model()}
+
+
+def _cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (x86 model name, or the Arm
+    implementer / part codes), with the logical core count."""
+    name = None
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+        for key in ("model name", "Model name"):
+            hits = [l.split(":", 1)[1].strip() for l in info if l.startswith(key)]
+            if hits:
+                name = hits[0]
+                break
+        if name is None:
+            imp = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU implementer")]
+            part = [l.split(":", 1)[1].strip() for l in info if l.startswith("CPU part")]
+            if imp and part:
+                name = f"Arm implementer {imp[0]} part {part[0]}"
+    except OSError:
+        pass
+    return f"{name or platform.machine()}, {os.cpu_count()} logical cores"
 
 
 def run_ours(args):

@@ -81,8 +81,16 @@ def _load():
         lib.orc_backproject_pixels.restype = ci
         lib.orc_trace_one.argtypes = [ci, cd, cd, cd, cd, i32p, f64p]
         lib.orc_trace_one.restype = ci
+        lib.orc_set_threads.argtypes = [ci]
+        lib.orc_set_threads.restype = ci
         _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the C part's OpenMP loops (0: leave as is); returns the
+    previous count."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 # --------------------------------------------------------------------------

@@ -24,6 +24,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ------------------------------------------------------------------------ */
 /* Siddon ray trace (classic form).                                          */
@@ -340,3 +343,17 @@ int orc_trace_one(int n, double c, double s, double t, double min_seg,
   free(ent);
   return cnt;
 }
+
+/* Threads of the OpenMP loops (timing on one core or on all of them);
+ * returns the previous setting. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  int prev = omp_get_max_threads();
+  if (n > 0) omp_set_num_threads(n);
+  return prev;
+#else
+  (void)n;
+  return 1;
+#endif
+}
+
