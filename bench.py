@@ -823,8 +823,9 @@ def run_cusparse(args):
 
 
 def run_matfree(args):
-    """Memoized against matrix-free projection (Sec. II-B's argument for
-    memoizing A), 512^2 x 768 x 512, FP32 and binary16 plans."""
+    """Memoized against matrix-free projection and back projection (Sec.
+    II-B's argument for memoizing A), 512^2 x 768 x 512, FP32 and binary16
+    plans."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__
@@ -856,9 +857,18 @@ def run_matfree(args):
             t_mf = timed(lambda: xct.xct_project_matfree(p32.handle, x, y, S), max(1, args.steps // 3))
             t32 = timed(lambda: p32.project(x, out=y), args.steps)
             t16 = timed(lambda: p16.project(x, out=y), args.steps)
+            # back projection: pixel by pixel without the matrix
+            t_bmf = timed(lambda: xct.xct_backproject_matfree(p32.handle, y, x, S),
+                          max(1, args.steps // 3))
+            tb32 = timed(lambda: p32.backproject(y, out=x), args.steps)
+            tb16 = timed(lambda: p16.backproject(y, out=x), args.steps)
             out[f"S{S}"] = {"matfree_ms": t_mf, "memoized_f32_ms": t32, "memoized_f16_ms": t16,
                             "matfree_gflops": 2.0 * nnz * S / (t_mf * 1e-3) / 1e9,
-                            "speedup_memoized_f32": t_mf / t32, "speedup_memoized_f16": t_mf / t16}
+                            "speedup_memoized_f32": t_mf / t32, "speedup_memoized_f16": t_mf / t16,
+                            "back_matfree_ms": t_bmf, "back_memoized_f32_ms": tb32,
+                            "back_memoized_f16_ms": tb16,
+                            "back_matfree_gflops": 2.0 * nnz * S / (t_bmf * 1e-3) / 1e9,
+                            "back_speedup_memoized_f16": t_bmf / tb16}
     print(json.dumps(out))
 
 

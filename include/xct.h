@@ -139,6 +139,23 @@ xct_status xct_project_matfree(xct_plan_t plan, const float* x, float* y, int32_
                                void* stream);
 
 /*
+ * xct_backproject_matfree -- x = A^T y without the stored matrix, pixel by
+ * pixel: for each pixel and angle, the few rays whose line can meet the
+ * pixel are tested, and a ray's length in the pixel is taken from its
+ * crossings of the pixel's four boundary planes with the plan's FP64
+ * arithmetic -- the segment the trace of xct_plan keeps, so the lengths
+ * equal the stored FP64 values bit for bit (for min_seg > 0; with
+ * min_seg = 0 the trace also keeps slivers below 1e-14 left by rounding
+ * where two crossings coincide, which this rule does not).  RN32(length) * y is summed in
+ * FP32 over ascending ray ids, 8 slices per pass.  The transpose of
+ * xct_project_matfree; with it, CGLS needs no stored matrix (Sec. II-B's
+ * alternative to memoization).  y, x: natural layouts, host or device.
+ * Synchronous.
+ */
+xct_status xct_backproject_matfree(xct_plan_t plan, const float* y, float* x, int32_t S,
+                                   void* stream);
+
+/*
  * xct_project_f64 / xct_backproject_f64 / xct_cgls_f64 -- the double-precision
  * form that Sec. V measures the single, half and mixed forms against: the
  * plan's kept FP64 matrix values (the plan must be built with

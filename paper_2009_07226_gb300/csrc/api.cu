@@ -792,6 +792,32 @@ xct_status xct_cgls_f64(xct_plan_t plan, const double* y, double* x, int32_t S, 
   return XCT_OK;
 }
 
+xct_status xct_backproject_matfree(xct_plan_t plan, const float* y, float* x, int32_t S,
+                                   void* stream) {
+  XCT_TRY(check_plan(plan));
+  if (S < 0 || ((!x || !y) && S > 0)) {
+    set_error("bad arguments (S = %d)", S);
+    return XCT_ERR_INVALID;
+  }
+  if (S == 0) return XCT_OK;
+  Plan& p = *plan;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  Arena ar(s);
+  DevView yv, xv;
+  XCT_TRY(device_view(y, (size_t)S * p.nray, true, ar, s, yv));
+  XCT_TRY(device_view(x, (size_t)S * p.npix, false, ar, s, xv));
+  double* cs_dev;
+  XCT_TRY(ar.get(&cs_dev, 2 * (size_t)p.g.n_angles));
+  XCT_TRY_CUDA(cudaMemcpyAsync(cs_dev, p.cs.data(), sizeof(double) * 2 * p.g.n_angles,
+                               cudaMemcpyHostToDevice, s));
+  XCT_TRY(matfree_backproject(p, cs_dev, yv.dev, xv.dev, S, s));
+  if (xv.host) {
+    XCT_TRY_CUDA(cudaMemcpyAsync(x, xv.dev, sizeof(float) * S * p.npix, cudaMemcpyDeviceToHost, s));
+  }
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  return XCT_OK;
+}
+
 int64_t xct_cgls_state_bytes(xct_plan_t plan, int32_t S) {
   if (!plan || S < 1) return 0;
   return (int64_t)state_bytes(plan->npix, plan->nray, S);

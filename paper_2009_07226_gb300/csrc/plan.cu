@@ -1007,6 +1007,116 @@ xct_status time_product(const Layout& L, Plan& p, cudaStream_t s, double* ms_out
   return XCT_OK;
 }
 
+// Matrix-free back projection, pixel-driven: x[s][pixel] = sum over the rays
+// through the pixel, in ascending ray id, of RN32(length) * y[s][ray] in
+// FP32.  A ray's length in a pixel is its traced segment there, found
+// without tracing: the ray's crossings of the pixel's four boundary planes
+// (the same plane_alpha doubles the trace merges; planes 0 and n give the
+// slab clip's doubles) and the ray's clip interval bound it, no other
+// crossing lies strictly inside, and the trace keeps the segment when it is
+// at least min_seg long, assigning it to the pixel of its midpoint.  So the
+// lengths equal the stored matrix's values bit for bit (min_seg > 0; with
+// min_seg = 0 the trace also keeps the slivers, below 1e-14, that rounding
+// leaves between crossings which coincide in real arithmetic).
+__global__ void matfree_ray_setup_kernel(GeomDev g, int64_t nray, double4* rs) {
+  const int64_t ray = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (ray >= nray) return;
+  Ray r;
+  // amin > amax marks a ray that is not traced (it misses the grid or keeps
+  // less than min_seg of it)
+  rs[ray] = setup_row(g, (int32_t)ray, r) ? make_double4(r.px, r.py, r.amin, r.amax)
+                                          : make_double4(0.0, 0.0, 1.0, 0.0);
+}
+
+// the alpha interval of the ray inside pixel column (row) i of one axis;
+// false when the axis is parallel to the ray and the line is outside it
+__device__ __forceinline__ bool pixel_axis(int i, int n, double half, double p, double d,
+                                           double& lo, double& hi) {
+  if (d != 0.0) {
+    const double a0 = plane_alpha(i, half, p, d), a1 = plane_alpha(i + 1, half, p, d);
+    lo = a0 < a1 ? a0 : a1;
+    hi = a0 < a1 ? a1 : a0;
+    return true;
+  }
+  int c = (int)floor(dadd(p, half));
+  c = c < 0 ? 0 : (c > n - 1 ? n - 1 : c);
+  lo = -INFINITY;
+  hi = INFINITY;
+  return c == i;
+}
+
+__global__ void matfree_backproject_kernel(GeomDev g, const double4* rs, const float* y, float* x,
+                                           int S, int64_t nray) {
+  const int n = g.n;
+  const int64_t npix = (int64_t)n * n;
+  const int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  const int ix = (int)(pix % n), iy = (int)(pix / n);
+  const double half = dmul(0.5, (double)n);
+  // pixel centre, for the window of candidate bins only
+  const double xc = (double)ix - half + 0.5, yc = (double)iy - half + 0.5;
+  const double c0 = 0.5 * (double)(g.nd - 1);
+  for (int s0 = 0; s0 < S; s0 += kMfSlices) {
+    const int ns = min(kMfSlices, S - s0);
+    float acc[kMfSlices];
+#pragma unroll
+    for (int q = 0; q < kMfSlices; ++q) acc[q] = 0.0f;
+    for (int k = 0; k < g.m; ++k) {
+      const double c = g.cs[2 * k], sn = g.cs[2 * k + 1];
+      const double dx = -sn, dy = c;
+      // bins whose line can meet the pixel: |t_j - t_c| <= (|c| + |s|) / 2,
+      // one more bin on each side (the plane test below decides)
+      const double tc = xc * c + yc * sn, w = 0.5 * (fabs(c) + fabs(sn));
+      double jlo = (tc - w - g.doff) / g.dspace + c0, jhi = (tc + w - g.doff) / g.dspace + c0;
+      if (jlo > jhi) {
+        const double t = jlo;
+        jlo = jhi;
+        jhi = t;
+      }
+      const int j0 = max(0, (int)floor(jlo) - 1), j1 = min(g.nd - 1, (int)ceil(jhi) + 1);
+      for (int j = j0; j <= j1; ++j) {
+        const int64_t ray = (int64_t)k * g.nd + j;
+        const double4 q = rs[ray];   // px, py, amin, amax
+        if (!(q.z <= q.w)) continue;
+        double xlo, xhi, ylo, yhi;
+        if (!pixel_axis(ix, n, half, q.x, dx, xlo, xhi)) continue;
+        if (!pixel_axis(iy, n, half, q.y, dy, ylo, yhi)) continue;
+        double a = xlo > ylo ? xlo : ylo, b = xhi < yhi ? xhi : yhi;
+        a = a > q.z ? a : q.z;
+        b = b < q.w ? b : q.w;
+        const double len = dsub(b, a);
+        if (!(len >= g.min_seg)) continue;
+        const double mid = dmul(dadd(a, b), 0.5);
+        int px = (int)floor(dadd(dadd(q.x, dmul(mid, dx)), half));
+        int py = (int)floor(dadd(dadd(q.y, dmul(mid, dy)), half));
+        px = px < 0 ? 0 : (px > n - 1 ? n - 1 : px);
+        py = py < 0 ? 0 : (py > n - 1 ? n - 1 : py);
+        if (px != ix || py != iy) continue;
+        const float l = (float)len;
+#pragma unroll
+        for (int q2 = 0; q2 < kMfSlices; ++q2)
+          if (q2 < ns) acc[q2] = fmaf(l, __ldg(y + (size_t)(s0 + q2) * nray + ray), acc[q2]);
+      }
+    }
+    for (int q = 0; q < ns; ++q) x[(size_t)(s0 + q) * npix + pix] = acc[q];
+  }
+}
+
+xct_status matfree_backproject(const Plan& p, const double* cs_dev, const float* y, float* x, int S,
+                               cudaStream_t s) {
+  const xct_geometry& g = p.g;
+  GeomDev gd{g.n, g.n_angles, g.n_det, g.det_spacing, g.det_offset, g.min_seg, cs_dev};
+  Arena tmp(s);
+  double4* rs;
+  XCT_TRY(tmp.get(&rs, p.nray));
+  matfree_ray_setup_kernel<<<grid_for(p.nray, 256), 256, 0, s>>>(gd, p.nray, rs);
+  matfree_backproject_kernel<<<grid_for(p.npix, 128), 128, 0, s>>>(gd, rs, y, x, S, p.nray);
+  count_launch(2);
+  XCT_TRY_CUDA(cudaGetLastError());
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));   // rs is released next
+  return XCT_OK;
+}
+
 xct_status matfree_project(const Plan& p, const double* cs_dev, const float* x, float* y, int S,
                            cudaStream_t s) {
   const xct_geometry& g = p.g;

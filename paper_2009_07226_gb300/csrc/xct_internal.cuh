@@ -171,6 +171,10 @@ xct_status build_plan(Plan& p, cudaStream_t s);
 // y = A x without the stored matrix: every ray traced again (plan.cu)
 xct_status matfree_project(const Plan& p, const double* cs_dev, const float* x, float* y, int S,
                            cudaStream_t s);
+// x = A^T y without the stored matrix: pixel-driven, lengths from each
+// pixel's boundary planes, equal to the stored values (plan.cu)
+xct_status matfree_backproject(const Plan& p, const double* cs_dev, const float* y, float* x, int S,
+                               cudaStream_t s);
 // the double-precision form (f64.cu): products and CGLS on the kept FP64
 // matrices, natural-layout device vectors; f64_cgls writes log [iters+1][S][2]
 // (device, nullable) and whether any slice was active after the start

@@ -103,6 +103,8 @@ _SIGNATURES = [
     ("xct_cgls_state_bytes", ctypes.c_int64, [ctypes.c_void_p, ctypes.c_int32]),
     ("xct_project_matfree", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                            ctypes.c_int32, ctypes.c_void_p]),
+    ("xct_backproject_matfree", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int32, ctypes.c_void_p]),
     ("xct_cgls_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
@@ -232,6 +234,10 @@ def xct_cgls_f64(plan: int, y, x, S: int, iters: int, flags: int = 0, resid=None
                  stream=None) -> None:
     _check(lib().xct_cgls_f64(plan, _ptr(y), _ptr(x), S, iters, flags, _ptr(resid),
                               _stream(stream)))
+
+
+def xct_backproject_matfree(plan: int, y, x, S: int, stream=None) -> None:
+    _check(lib().xct_backproject_matfree(plan, _ptr(y), _ptr(x), S, _stream(stream)))
 
 
 def xct_cgls_state_bytes(plan: int, S: int) -> int:
