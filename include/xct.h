@@ -156,6 +156,17 @@ xct_status xct_backproject_matfree(xct_plan_t plan, const float* y, float* x, in
                                    void* stream);
 
 /*
+ * xct_cgls_matfree -- xct_cgls with the matrix-free products above (no
+ * stored matrix is read): the same recurrence, FP32 vectors and FP64
+ * per-slice scalars, the same stop and XCT_ERR_BREAKDOWN rules, resid as
+ * there; flags: XCT_CGLS_X0 only.  Each product traces the geometry again,
+ * so a solve costs hundreds of times the memoized one (Sec. II-B); it is
+ * the form for grids whose matrix does not fit.  Synchronous.
+ */
+xct_status xct_cgls_matfree(xct_plan_t plan, const float* y, float* x, int32_t S,
+                            int32_t iters, uint32_t flags, double* resid, void* stream);
+
+/*
  * xct_project_f64 / xct_backproject_f64 / xct_cgls_f64 -- the double-precision
  * form that Sec. V measures the single, half and mixed forms against: the
  * plan's kept FP64 matrix values (the plan must be built with

@@ -818,6 +818,95 @@ xct_status xct_backproject_matfree(xct_plan_t plan, const float* y, float* x, in
   return XCT_OK;
 }
 
+xct_status xct_cgls_matfree(xct_plan_t plan, const float* y, float* x, int32_t S, int32_t iters,
+                            uint32_t flags, double* resid, void* stream) {
+  XCT_TRY(check_plan(plan));
+  if (S < 0 || iters < 0 || ((!x || !y) && S > 0)) {
+    set_error("bad arguments (S = %d, iters = %d)", S, iters);
+    return XCT_ERR_INVALID;
+  }
+  if (flags & ~XCT_CGLS_X0) {
+    set_error("unknown matrix-free CGLS flags 0x%x", flags);
+    return XCT_ERR_INVALID;
+  }
+  if (S == 0) return XCT_OK;
+  Plan& p = *plan;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool x0 = (flags & XCT_CGLS_X0) != 0;
+  const int64_t npix = p.npix, nray = p.nray;
+  Arena ar(s);
+  DevView yv, xv;
+  XCT_TRY(device_view(y, (size_t)S * nray, true, ar, s, yv));
+  XCT_TRY(device_view(x, (size_t)S * npix, x0, ar, s, xv));
+  double* cs_dev;
+  XCT_TRY(ar.get(&cs_dev, 2 * (size_t)p.g.n_angles));
+  XCT_TRY_CUDA(cudaMemcpyAsync(cs_dev, p.cs.data(), sizeof(double) * 2 * p.g.n_angles,
+                               cudaMemcpyHostToDevice, s));
+  // natural layouts are the vector kernels' layout with one slice per tile
+  float *X, *P, *Sv, *R, *Q;
+  double *dpart, *gpart, *rpart, *log;
+  CglsScalars sc{};
+  XCT_TRY(ar.get(&X, (size_t)npix * S));
+  XCT_TRY(ar.get(&P, (size_t)npix * S));
+  XCT_TRY(ar.get(&Sv, (size_t)npix * S));
+  XCT_TRY(ar.get(&R, (size_t)nray * S));
+  XCT_TRY(ar.get(&Q, (size_t)nray * S));
+  XCT_TRY(ar.get(&dpart, (size_t)S * kVecBlocks));
+  XCT_TRY(ar.get(&gpart, (size_t)S * kVecBlocks));
+  XCT_TRY(ar.get(&rpart, (size_t)S * kVecBlocks));
+  XCT_TRY(ar.get(&log, (size_t)(iters + 1) * S * 2));
+  XCT_TRY(ar.get(&sc.gamma, (size_t)S));
+  XCT_TRY(ar.get(&sc.alpha, (size_t)S));
+  XCT_TRY(ar.get(&sc.beta, (size_t)S));
+  XCT_TRY(ar.get(&sc.active, (size_t)S));
+  XCT_TRY(ar.get(&sc.active0, (size_t)S));
+  XCT_TRY(ar.get(&sc.max_r, (size_t)S));
+  XCT_TRY(ar.get(&sc.max_p, (size_t)S));
+  // the recurrence of xct_cgls (Table IV footnote: one initial back
+  // projection, then one projection and one back projection per iteration)
+  XCT_TRY_CUDA(cudaMemcpyAsync(R, yv.dev, sizeof(float) * nray * S, cudaMemcpyDeviceToDevice, s));
+  if (x0) {
+    XCT_TRY_CUDA(cudaMemcpyAsync(X, xv.dev, sizeof(float) * npix * S, cudaMemcpyDeviceToDevice, s));
+    XCT_TRY(matfree_project(p, cs_dev, X, Q, S, s));
+    XCT_TRY(cgls_residual(R, Q, nray, 1, S, sc.max_r, rpart, s));
+  } else {
+    XCT_TRY_CUDA(cudaMemsetAsync(X, 0, sizeof(float) * npix * S, s));
+    XCT_TRY(cgls_residual(R, nullptr, nray, 1, S, sc.max_r, rpart, s));
+  }
+  XCT_TRY(matfree_backproject(p, cs_dev, R, Sv, S, s));
+  XCT_TRY(cgls_residual(Sv, nullptr, npix, 1, S, sc.max_p, gpart, s));
+  XCT_TRY(cgls_init_scalars(gpart, kVecBlocks, rpart, sc, log, S, s));
+  XCT_TRY_CUDA(cudaMemsetAsync(P, 0, sizeof(float) * npix * S, s));
+  XCT_TRY(cgls_update_p(P, Sv, npix, 1, S, sc, s));
+  for (int it = 1; it <= iters; ++it) {
+    XCT_TRY(matfree_project(p, cs_dev, P, Q, S, s));
+    XCT_TRY(cgls_residual(Q, nullptr, nray, 1, S, sc.max_r, dpart, s));
+    XCT_TRY(cgls_alpha(dpart, kVecBlocks, sc, S, s));
+    XCT_TRY(cgls_update_xr(X, P, npix, R, Q, nray, 1, S, sc, rpart, s));
+    XCT_TRY(matfree_backproject(p, cs_dev, R, Sv, S, s));
+    XCT_TRY(cgls_residual(Sv, nullptr, npix, 1, S, sc.max_p, gpart, s));
+    XCT_TRY(cgls_beta(gpart, kVecBlocks, rpart, sc, log + (size_t)it * S * 2, S, s));
+    XCT_TRY(cgls_update_p(P, Sv, npix, 1, S, sc, s));
+  }
+  XCT_TRY_CUDA(cudaMemcpyAsync(xv.dev, X, sizeof(float) * npix * S, cudaMemcpyDeviceToDevice, s));
+  if (xv.host)
+    XCT_TRY_CUDA(cudaMemcpyAsync(x, xv.dev, sizeof(float) * S * npix, cudaMemcpyDeviceToHost, s));
+  if (resid)
+    XCT_TRY_CUDA(cudaMemcpyAsync(resid, log, sizeof(double) * (iters + 1) * S * 2,
+                                 is_host_pointer(resid) ? cudaMemcpyDeviceToHost
+                                                        : cudaMemcpyDeviceToDevice, s));
+  std::vector<int> act0((size_t)S);
+  XCT_TRY_CUDA(cudaMemcpyAsync(act0.data(), sc.active0, sizeof(int) * S, cudaMemcpyDeviceToHost, s));
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  bool any = false;
+  for (int i = 0; i < S; ++i) any = any || act0[i];
+  if (!any) {
+    set_error("CGLS breakdown: every slice has A^T r_0 = 0");
+    return XCT_ERR_BREAKDOWN;
+  }
+  return XCT_OK;
+}
+
 int64_t xct_cgls_state_bytes(xct_plan_t plan, int32_t S) {
   if (!plan || S < 1) return 0;
   return (int64_t)state_bytes(plan->npix, plan->nray, S);

@@ -105,6 +105,9 @@ _SIGNATURES = [
                                            ctypes.c_int32, ctypes.c_void_p]),
     ("xct_backproject_matfree", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                ctypes.c_int32, ctypes.c_void_p]),
+    ("xct_cgls_matfree", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_int32, ctypes.c_int32, ctypes.c_uint32,
+                                        ctypes.c_void_p, ctypes.c_void_p]),
     ("xct_cgls_state", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                       ctypes.c_int32, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                       ctypes.c_void_p]),
@@ -238,6 +241,12 @@ def xct_cgls_f64(plan: int, y, x, S: int, iters: int, flags: int = 0, resid=None
 
 def xct_backproject_matfree(plan: int, y, x, S: int, stream=None) -> None:
     _check(lib().xct_backproject_matfree(plan, _ptr(y), _ptr(x), S, _stream(stream)))
+
+
+def xct_cgls_matfree(plan: int, y, x, S: int, iters: int, flags: int = 0, resid=None,
+                     stream=None) -> None:
+    _check(lib().xct_cgls_matfree(plan, _ptr(y), _ptr(x), S, iters, flags, _ptr(resid),
+                                  _stream(stream)))
 
 
 def xct_cgls_state_bytes(plan: int, S: int) -> int:

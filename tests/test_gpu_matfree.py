@@ -129,3 +129,66 @@ def test_matfree_backprojection_lengths_are_the_stored_values(xct, n, m, nd, off
         assert np.array_equal(x, dense)
     else:
         assert np.abs(x - dense).max() <= 1e-14
+
+
+# ---------------------------------------------------------------------------
+# CGLS without a stored matrix
+# ---------------------------------------------------------------------------
+
+def _ops(a, at):
+    return (lambda X: oracle.project(a, X)), (lambda Y: oracle.backproject(at, Y))
+
+
+def test_matfree_cgls_stable_phase(xct):
+    """Same recurrence as xct_cgls on the memoized FP32 plan: within the
+    FP32 envelope of the FP64 oracle over the stable phase (k <= 5), and
+    of the memoized solve."""
+    w = inputs.make_workload("cgls2d_128")
+    n, m, nd = w["n"], w["m"], w["nd"]
+    g = oracle.Geometry(n=n, m=m, nd=nd, cos_sin=w["cos_sin"])
+    a = oracle.siddon_csr(g)
+    at = oracle.transpose(a)
+    b = oracle.project(a, w["images"].reshape(1, -1))
+    bt = torch.tensor(b.reshape(1, m, nd), dtype=torch.float32, device="cuda")
+    with xct.Plan(n, m, nd, "f32", cos_sin=g.table()) as p:
+        for k in (1, 3, 5):
+            x = torch.empty((1, n, n), device="cuda")
+            log = torch.zeros((k + 1, 1, 2), dtype=torch.float64, device="cuda")
+            xct.xct_cgls_matfree(p.handle, bt, x, 1, k, 0, log)
+            xm, lm = p.cgls(bt, k, resid=True)
+            xr, lr = oracle.cgls(*_ops(a, at), b, k)
+            got = x.cpu().numpy().reshape(1, -1)
+            assert np.linalg.norm(got - xr) / np.linalg.norm(xr) <= 2e-5, k
+            assert np.linalg.norm(got - xm.cpu().numpy().reshape(1, -1)) / np.linalg.norm(xr) <= 2e-5
+            np.testing.assert_allclose(log.cpu().numpy(), lr, rtol=2e-5)
+
+
+def test_matfree_cgls_x0_stop_and_breakdown(xct):
+    n, m, nd, S, k = 24, 30, 26, 3, 3
+    g = oracle.Geometry(n=n, m=m, nd=nd, cos_sin=inputs.angle_table(m))
+    a = oracle.siddon_csr(g)
+    at = oracle.transpose(a)
+    rng = np.random.default_rng(7)
+    b = (oracle.project(a, rng.random((S, n * n))) + 0.01 * rng.standard_normal((S, m * nd)))
+    b[1] = 0.0
+    b = b.astype(np.float32).astype(np.float64)
+    x0 = (0.1 * rng.random((S, n * n))).astype(np.float32)
+    x0[1] = 0.0
+    with xct.Plan(n, m, nd, "f16", cos_sin=g.table()) as p:
+        # host buffers, start from x0
+        xh = x0.reshape(S, n, n).copy()
+        log = np.zeros((k + 1, S, 2))
+        xct.xct_cgls_matfree(p.handle, b.astype(np.float32).reshape(S, m, nd), xh, S, k,
+                             xct.XCT_CGLS_X0, log)
+        xr, lr = oracle.cgls(*_ops(a, at), b, k, x0=x0.astype(np.float64))
+        got = xh.reshape(S, -1).astype(np.float64)
+        assert np.array_equal(got[1], x0[1])
+        for s in (0, 2):
+            assert np.linalg.norm(got[s] - xr[s]) / np.linalg.norm(xr[s]) <= 2e-5
+        np.testing.assert_allclose(log[:, [0, 2]], lr[:, [0, 2]], rtol=2e-5)
+        # zero data: every slice stops at k = 0
+        with pytest.raises(xct.XctError) as e:
+            xz = torch.full((2, n, n), 5.0, device="cuda")
+            xct.xct_cgls_matfree(p.handle, torch.zeros((2, m, nd), device="cuda"), xz, 2, 2)
+        assert e.value.status == xct.XCT_ERR_BREAKDOWN
+        assert torch.count_nonzero(xz) == 0
