@@ -147,6 +147,13 @@ def _oracle_step(a, at, b, iters):
     oracle.cgls(lambda X: oracle.project(a, X), lambda Y: oracle.backproject(at, Y), b, iters)
 
 
+def _config(n, m, nd, S, K, nnz, world):
+    """The workload of the JSON line (both arms)."""
+    return {"workload": WORKLOAD, "n": n, "angles": m, "bins": nd, "slices_per_gpu": S,
+            "iters": K, "nnz": nnz, "l2": "inputs larger than L2 (packed A 1.2 GB per product)",
+            "parallelism": f"slice-sharded x{world}, no collective"}
+
+
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
@@ -165,15 +172,16 @@ def run_reference(args):
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
     flops = (2 * iters + 1) * 2.0 * nnz * 1
     gf = flops / dt / 1e9
-    cores = os.cpu_count()
+    import oracle
+    cores = oracle.set_threads(0)
     sample = f"1 of 64 slices, {iters} CGLS iterations per step (FP64, CSR oracle)"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": gf, "unit": "GFLOP/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": w["n"], "angles": w["m"], "bins": w["nd"],
-                   "slices": 1, "iters": iters},
+        "config": _config(w["n"], w["m"], w["nd"], inputs.WORKLOADS[WORKLOAD]["slices"],
+                          inputs.WORKLOADS[WORKLOAD]["iters"], nnz, world),
         "cpu_baseline": {"value": gf, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": gf, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -423,9 +431,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms16,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16",
         "data": "synthetic (seeded ellipsoid phantom, exact line integrals, Poisson 1e4)",
-        "config": {"workload": WORKLOAD, "n": n, "angles": m, "bins": nd, "slices_per_gpu": S,
-                   "iters": K, "nnz": nnz, "l2": "inputs larger than L2 (packed A 1.2 GB per product)",
-                   "parallelism": f"slice-sharded x{world}, no collective"},
+        "config": _config(n, m, nd, S, K, nnz, world),
         "fp32": {"value": flops_step / (ms32 * 1e-3) / 1e9, "unit": "GFLOP/s", "ms_per_step": ms32,
                  "cgls_iter_per_s": K / (ms32 * 1e-3)},
         "speedup_mixed_vs_fp32": ms32 / ms16,
