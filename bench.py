@@ -875,6 +875,20 @@ def run_matfree(args):
                             "back_memoized_f16_ms": tb16,
                             "back_matfree_gflops": 2.0 * nnz * S / (t_bmf * 1e-3) / 1e9,
                             "back_speedup_memoized_f16": t_bmf / tb16}
+        # CGLS without the stored matrix: 8 slices, 3 iterations (7 products)
+        S, K = 8, 3
+        g = torch.Generator(device="cuda").manual_seed(1)
+        y8 = torch.rand((S, m, nd), device="cuda", generator=g)
+        x8 = torch.empty((S, n, n), device="cuda")
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record()
+        xct.xct_cgls_matfree(p32.handle, y8, x8, S, K)
+        ev[1].record()
+        xct.xct_cgls(p16.handle, y8, x8, S, K, 0, None)
+        ev[2].record()
+        torch.cuda.synchronize()
+        out["cgls_S8_3iters"] = {"matfree_ms": ev[0].elapsed_time(ev[1]),
+                                 "memoized_f16_ms": ev[1].elapsed_time(ev[2])}
     print(json.dumps(out))
 
 
