@@ -490,14 +490,16 @@ def run_ours(args):
 
 def run_products(args):
     """Projection and back projection alone (S = 64 slices of the workload's
-    geometry, one storage type): for profiling the product kernels."""
+    geometry unless --slices says otherwise, one storage type): for
+    profiling the product kernels."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
     from paper_2009_07226_gb300 import inputs, xct
     wl = inputs.WORKLOADS[WORKLOAD]
-    n, m, nd, S = wl["n"], wl["m"], wl["nd"], wl["slices"]
+    n, m, nd = wl["n"], wl["m"], wl["nd"]
+    S = args.slices or wl["slices"]
     plan = xct.Plan(n, m, nd, args.storage, cos_sin=inputs.angle_table(m))
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.rand((S, n, n), device="cuda", generator=g)
@@ -908,6 +910,8 @@ def main():
     ap.add_argument("--mode", default="cgls", choices=["cgls", "products", "batch", "tv", "large", "cusparse", "matfree",
                              "pipeline"])
     ap.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16", "f16a", "bf16a"])
+    ap.add_argument("--slices", type=int, default=0,
+                    help="--mode products: slices per product (default: the workload's 64)")
     args = ap.parse_args()
     if args.mode == "products":
         run_products(args)
