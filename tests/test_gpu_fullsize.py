@@ -88,3 +88,20 @@ def test_cgls_sampled_slices(xct):
         # with the 16-bit product, the recomputation uses the FP64 matrix
         rtol = 1e-3 if kind == "f32" else 1e-2
         assert np.all(np.abs(got_r - true_r) <= rtol * true_r), (kind, got_r, true_r)
+
+
+def test_fp64_products_sampled(xct, setup):
+    """The double-precision form at full size: sampled rays and pixels
+    against the oracle within the FP64 summation bound (inputs and lengths
+    are non-negative, so sum |a x| is the output itself): 2 gamma_n with n
+    up to 2 * 512 * 1.5 terms per output, under 4e-13 relative."""
+    g, x, y, rays, pixels, ref_y, ref_x = setup
+    with xct.Plan(N, M, ND, "f16", cos_sin=g.table(), keep_f64=True) as p:
+        yo = p.project_f64(torch.tensor(x.reshape(S, N, N), dtype=torch.float64, device="cuda"))
+        xo = p.backproject_f64(torch.tensor(y.reshape(S, M, ND), dtype=torch.float64,
+                                            device="cuda"))
+        torch.cuda.synchronize()
+    gy = yo.reshape(S, -1)[:, torch.tensor(rays, device="cuda")].cpu().numpy()
+    gx = xo.reshape(S, -1)[:, torch.tensor(pixels, device="cuda")].cpu().numpy()
+    for got, ref in ((gy, ref_y), (gx, ref_x)):
+        assert np.all(np.abs(got - ref) <= 4e-13 * ref + 1e-300)
