@@ -8,6 +8,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "xct_internal.cuh"
 #include "xct_vec.cuh"
 
@@ -568,6 +570,15 @@ xct_status apply_impl(Plan& p, bool transposed, const float* in, float* out, int
 
 bool is_finite_d(double v) { return isfinite(v) != 0; }
 
+// An NVTX range for the duration of an entry point (a no-op unless a
+// profiler is attached), so traces show the library's calls by name.
+struct Trace {
+  explicit Trace(const char* name) { nvtxRangePushA(name); }
+  ~Trace() { nvtxRangePop(); }
+  Trace(const Trace&) = delete;
+  Trace& operator=(const Trace&) = delete;
+};
+
 }  // namespace
 }  // namespace xct
 
@@ -577,6 +588,7 @@ extern "C" {
 
 xct_status xct_plan(const xct_geometry* g, xct_dtype storage, uint32_t flags, void* stream,
                     xct_plan_t* out) {
+  Trace trace_("xct_plan");
   if (!out) {
     set_error("out is NULL");
     return XCT_ERR_INVALID;
@@ -655,6 +667,7 @@ void xct_free(xct_plan_t plan) {
 }
 
 xct_status xct_project(xct_plan_t plan, const float* x, float* y, int32_t S, void* stream) {
+  Trace trace_("xct_project");
   XCT_TRY(check_plan(plan));
   if (S < 0 || ((!x || !y) && S > 0)) {
     set_error("bad arguments (S = %d)", S);
@@ -665,6 +678,7 @@ xct_status xct_project(xct_plan_t plan, const float* x, float* y, int32_t S, voi
 }
 
 xct_status xct_backproject(xct_plan_t plan, const float* y, float* x, int32_t S, void* stream) {
+  Trace trace_("xct_backproject");
   XCT_TRY(check_plan(plan));
   if (S < 0 || ((!x || !y) && S > 0)) {
     set_error("bad arguments (S = %d)", S);
@@ -676,6 +690,7 @@ xct_status xct_backproject(xct_plan_t plan, const float* y, float* x, int32_t S,
 
 xct_status xct_cgls(xct_plan_t plan, const float* y, float* x, int32_t S, int32_t iters,
                     uint32_t flags, double* resid, void* stream) {
+  Trace trace_("xct_cgls");
   XCT_TRY(check_plan(plan));
   if (S < 0 || iters < 0 || ((!x || !y) && S > 0)) {
     set_error("bad arguments (S = %d, iters = %d)", S, iters);
@@ -690,6 +705,7 @@ xct_status xct_cgls(xct_plan_t plan, const float* y, float* x, int32_t S, int32_
 }
 
 xct_status xct_project_matfree(xct_plan_t plan, const float* x, float* y, int32_t S, void* stream) {
+  Trace trace_("xct_project_matfree");
   XCT_TRY(check_plan(plan));
   if (S < 0 || ((!x || !y) && S > 0)) {
     set_error("bad arguments (S = %d)", S);
@@ -743,16 +759,19 @@ static xct_status apply_f64(xct_plan_t plan, bool transposed, const double* in, 
 }
 
 xct_status xct_project_f64(xct_plan_t plan, const double* x, double* y, int32_t S, void* stream) {
+  Trace trace_("xct_project_f64");
   return apply_f64(plan, false, x, y, S, stream);
 }
 
 xct_status xct_backproject_f64(xct_plan_t plan, const double* y, double* x, int32_t S,
                                void* stream) {
+  Trace trace_("xct_backproject_f64");
   return apply_f64(plan, true, y, x, S, stream);
 }
 
 xct_status xct_cgls_f64(xct_plan_t plan, const double* y, double* x, int32_t S, int32_t iters,
                         uint32_t flags, double* resid, void* stream) {
+  Trace trace_("xct_cgls_f64");
   XCT_TRY(check_plan(plan));
   if (S < 0 || iters < 0 || ((!x || !y) && S > 0)) {
     set_error("bad arguments (S = %d, iters = %d)", S, iters);
@@ -794,6 +813,7 @@ xct_status xct_cgls_f64(xct_plan_t plan, const double* y, double* x, int32_t S, 
 
 xct_status xct_backproject_matfree(xct_plan_t plan, const float* y, float* x, int32_t S,
                                    void* stream) {
+  Trace trace_("xct_backproject_matfree");
   XCT_TRY(check_plan(plan));
   if (S < 0 || ((!x || !y) && S > 0)) {
     set_error("bad arguments (S = %d)", S);
@@ -820,6 +840,7 @@ xct_status xct_backproject_matfree(xct_plan_t plan, const float* y, float* x, in
 
 xct_status xct_cgls_matfree(xct_plan_t plan, const float* y, float* x, int32_t S, int32_t iters,
                             uint32_t flags, double* resid, void* stream) {
+  Trace trace_("xct_cgls_matfree");
   XCT_TRY(check_plan(plan));
   if (S < 0 || iters < 0 || ((!x || !y) && S > 0)) {
     set_error("bad arguments (S = %d, iters = %d)", S, iters);
@@ -914,6 +935,7 @@ int64_t xct_cgls_state_bytes(xct_plan_t plan, int32_t S) {
 
 xct_status xct_cgls_state(xct_plan_t plan, const float* y, float* x, int32_t S, int32_t iters,
                           uint32_t flags, double* resid, void* state, void* stream) {
+  Trace trace_("xct_cgls_state");
   XCT_TRY(check_plan(plan));
   const uint32_t known = XCT_CGLS_X0 | XCT_CGLS_NO_GRAPH | XCT_CGLS_TIMING | XCT_CGLS_SAVE |
                          XCT_CGLS_RESUME;
