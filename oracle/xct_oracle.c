@@ -240,6 +240,7 @@ int orc_project_rays(int n, int m, int nd, const double* cs, double dspace,
                      double doff, double min_seg, int nslice, const double* X,
                      const int64_t* rays, int64_t count, double* Y) {
   int fail = 0;
+  (void)m;   /* the ray ids carry the angle; m is kept for a uniform signature */
   const int64_t npix = (int64_t)n * n;
 #pragma omp parallel reduction(| : fail)
   {
