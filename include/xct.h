@@ -353,21 +353,29 @@ xct_status xct_set_allocator(xct_alloc_fn alloc, xct_free_fn release, void* ctx)
 
 /*
  * xct_project_noalloc -- the projection of xct_project (same arithmetic, same
- * result) for callers that must not allocate device memory during the call:
- * processes whose device memory is owned up front by another component (a
- * serving runtime or a framework allocator that reserved the whole budget)
- * and latency-critical loops where an allocation could block or fail at an
- * unpredictable moment.  The paper has no counterpart; it is a service of this
- * library.  All working memory comes from one fixed device array of 32 MiB
- * that every GPU loading the library holds until the process exits; a call
- * whose working memory (S padded to the slice tile, times 4 bytes per pixel
- * and per ray, plus 2 bytes per pixel for 16-bit storage) exceeds it returns
- * XCT_ERR_INVALID.  x and y must be device pointers (XCT_ERR_INVALID
- * otherwise).  The array's device address is looked up on the first call made
- * on each device (with that device current); make that first call before any
- * stream capture.  Calls share the array: calls whose GPU work overlaps (on
- * several streams or host threads) race and must be serialised by the caller.
- * It calls no allocator of any kind.
+ * result, bit for bit) for callers that must not allocate device memory
+ * during the call: processes whose device memory is owned up front by another
+ * component (a serving runtime or a framework allocator that reserved the
+ * whole budget) and latency-critical loops where an allocation could block or
+ * fail at an unpredictable moment.  The paper has no counterpart; it is a
+ * service of this library.
+ *
+ * All working memory comes from one fixed device array of 32 MiB
+ * (33,554,432 bytes).  It becomes resident on a device when xct_plan builds
+ * a plan there (its address is looked up then, with the plan's device
+ * current), or at the latest on the first xct_project_noalloc call on that
+ * device, and stays until the process exits.  With st the slice tile the
+ * library picks for S (1, 2, 4, ..., 64 for XCT_F16 / XCT_BF16, up to 32
+ * otherwise, at least 8 for XCT_F16A / XCT_BF16A) and S_pad = st *
+ * ceil(S / st), a call needs, each term rounded up to a multiple of 256
+ * bytes: 4 * S_pad * n*n (input) + 4 * S_pad * M*N_d (output) + 2 * S_pad *
+ * n*n (XCT_F16 and XCT_BF16 only: the 16-bit copy) + 4 * S_pad (per-slice
+ * maxima) + 256 (work counter).  A call needing more returns XCT_ERR_INVALID
+ * before any work.  x and y must be device pointers (XCT_ERR_INVALID
+ * otherwise); the work runs on the plan's device (made current for the call,
+ * then restored).  Calls share the array: calls whose GPU work overlaps (on
+ * several streams or host threads) race and must be serialised by the
+ * caller.  It calls no allocator of any kind.
  */
 xct_status xct_project_noalloc(xct_plan_t plan, const float* x, float* y, int32_t S,
                                void* stream);

@@ -570,15 +570,6 @@ xct_status apply_impl(Plan& p, bool transposed, const float* in, float* out, int
 
 bool is_finite_d(double v) { return isfinite(v) != 0; }
 
-// An NVTX range for the duration of an entry point (a no-op unless a
-// profiler is attached), so traces show the library's calls by name.
-struct Trace {
-  explicit Trace(const char* name) { nvtxRangePushA(name); }
-  ~Trace() { nvtxRangePop(); }
-  Trace(const Trace&) = delete;
-  Trace& operator=(const Trace&) = delete;
-};
-
 }  // namespace
 }  // namespace xct
 
@@ -655,6 +646,11 @@ xct_status xct_plan(const xct_geometry* g, xct_dtype storage, uint32_t flags, vo
     cudaStreamSynchronize(s);
     return st;
   }
+  // the fixed array of xct_project_noalloc is loaded with its module on first
+  // use; taking its address here makes it resident on this device while the
+  // caller is still allowed to allocate (a failure here is reported again,
+  // and only, by xct_project_noalloc)
+  noalloc_reserve(p->device);
   *out = p.release();
   return XCT_OK;
 }

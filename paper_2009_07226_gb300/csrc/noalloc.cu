@@ -11,13 +11,18 @@
 // touches only memory that exists before the call: the plan, the caller's
 // buffers and the array below.
 //
-// The array holds kNoAllocBytes (32 MiB) on every GPU that loads the library,
-// until the process exits.  Its host-side name is only a stand-in for the
-// device symbol, so its device address is looked up once per device with
-// cudaGetSymbolAddress (on the first call made with that device current) and
-// cached.  All calls share the array and it keeps the last call's contents:
-// everything that must start at zero is cleared by each call, and calls whose
-// GPU work overlaps (several streams, several host threads) race on it.
+// The array holds kNoAllocBytes (32 MiB) per GPU.  CUDA loads a module's
+// device variables with the module, and by default (lazy loading) a module is
+// loaded on its first use; this file has no kernels, so its first use is the
+// address lookup.  xct_plan therefore looks the address up on the plan's
+// device (noalloc_reserve): from then on the array is resident on that device
+// until the process exits, and a no-allocation call finds it in place.  Its
+// host-side name is only a stand-in for the device symbol, so the device
+// address comes from cudaGetSymbolAddress, made with the device current, and
+// is cached per device.  All calls share the array and it keeps the last
+// call's contents: everything that must start at zero is cleared by each
+// call, and calls whose GPU work overlaps (several streams, several host
+// threads) race on it.
 #include <mutex>
 
 #include "xct_internal.cuh"
@@ -28,13 +33,25 @@ namespace {
 constexpr size_t kNoAllocBytes = (size_t)32 << 20;
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[kMaxDevices] = {};
 
-xct_status scratch_address(void** out) {
-  int dev = 0;
-  XCT_TRY_CUDA(cudaGetDevice(&dev));
+// Makes `dev` current for its lifetime and restores the previous device.
+struct DeviceGuard {
+  int prev = -1;
+  xct_status enter(int dev) {
+    XCT_TRY_CUDA(cudaGetDevice(&prev));
+    if (prev != dev) XCT_TRY_CUDA(cudaSetDevice(dev));
+    return XCT_OK;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// The array's address on `dev`, which must be the current device.
+xct_status scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= kMaxDevices) {
     set_error("device ordinal %d out of range", dev);
     return XCT_ERR_UNSUPPORTED;
@@ -66,11 +83,20 @@ bool device_accessible(const void* p) {
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 }  // namespace
+
+xct_status noalloc_reserve(int device) {
+  DeviceGuard g;
+  XCT_TRY(g.enter(device));
+  void* p = nullptr;
+  return scratch_address(device, &p);
+}
+
 }  // namespace xct
 
 extern "C" xct_status xct_project_noalloc(xct_plan_t plan, const float* x, float* y, int32_t S,
                                           void* stream) {
   using namespace xct;
+  Trace trace_("xct_project_noalloc");
   if (!plan) {
     set_error("plan is NULL");
     return XCT_ERR_INVALID;
@@ -81,6 +107,9 @@ extern "C" xct_status xct_project_noalloc(xct_plan_t plan, const float* x, float
   }
   if (S == 0) return XCT_OK;
   Plan& p = *static_cast<Plan*>(plan);
+  // the plan's matrices, the array and the launches all on the plan's device
+  DeviceGuard dg;
+  XCT_TRY(dg.enter(p.device));
   if (!device_accessible(x) || !device_accessible(y)) {
     set_error("xct_project_noalloc takes device pointers only (host buffers would need staging)");
     return XCT_ERR_INVALID;
@@ -104,7 +133,7 @@ extern "C" xct_status xct_project_noalloc(xct_plan_t plan, const float* x, float
     return XCT_ERR_INVALID;
   }
   void* base = nullptr;
-  XCT_TRY(scratch_address(&base));
+  XCT_TRY(scratch_address(p.device, &base));
   unsigned char* b = static_cast<unsigned char*>(base);
   float* Xi = reinterpret_cast<float*>(b);
   float* Yi = reinterpret_cast<float*>(b + b_xi);

@@ -10,6 +10,8 @@
 #include <map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "xct.h"
 
 namespace xct {
@@ -29,6 +31,20 @@ inline void count_launch(int64_t k = 1) { g_launches.fetch_add(k, std::memory_or
 // default).  Returns nullptr and sets the error message on failure.
 void* dalloc(size_t bytes, cudaStream_t s);
 void dfree(void* p, size_t bytes, cudaStream_t s);
+
+// An NVTX range for the duration of an entry point (a no-op unless a
+// profiler is attached), so traces show the library's calls by name.
+struct Trace {
+  explicit Trace(const char* name) { nvtxRangePushA(name); }
+  ~Trace() { nvtxRangePop(); }
+  Trace(const Trace&) = delete;
+  Trace& operator=(const Trace&) = delete;
+};
+
+// The fixed working array of xct_project_noalloc (noalloc.cu): resolve its
+// device address on `device` (made current for the call, then restored), so
+// that the array is resident there before the first call that relies on it.
+xct_status noalloc_reserve(int device);
 
 #define XCT_TRY_CUDA(call)                                                   \
   do {                                                                       \
