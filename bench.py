@@ -192,9 +192,31 @@ def run_reference(args):
 # our arm
 # --------------------------------------------------------------------------
 
-def cpu_baseline(w):
+def _cgls2d_vs_oracle(c1):
+    """The plain 2D workload's GPU solves against the FP64 oracle's CGLS of
+    the same (FP32-rounded) sinogram, projected by the oracle itself (30
+    iterations), and the oracle's own time."""
+    import oracle
+    xs, w = c1
+    a, at = _oracle_setup(w)
+    # the same consistent sinogram, from the oracle's own projector
+    b = oracle.project(a, w["images"].reshape(1, -1)).astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    xo, _ = oracle.cgls(lambda X: oracle.project(a, X), lambda Y: oracle.backproject(at, Y), b, w["iters"])
+    dt = time.perf_counter() - t0
+    out = {"oracle_ms_per_solve": dt * 1e3}
+    for kind, x in xs.items():
+        out[f"rel_err_{kind}_vs_oracle"] = float(np.linalg.norm(x - xo) / np.linalg.norm(xo))
+    ph = w["images"].reshape(1, -1)
+    out["phantom_rel_err"] = {"oracle": float(np.linalg.norm(xo - ph) / np.linalg.norm(ph)),
+                              **{k: float(np.linalg.norm(x - ph) / np.linalg.norm(ph)) for k, x in xs.items()}}
+    return out
+
+
+def cpu_baseline(w, c1=None):
     """The oracle, as it stands, on this host's cores: one slice, a few
-    iterations (a bounded sample of the same workload)."""
+    iterations (a bounded sample of the same workload); with c1, also the
+    plain 2D workload's solve checked against the oracle's."""
     import oracle
     a, at = _oracle_setup(w)
     b = w["sino"][:1].reshape(1, -1)
@@ -216,7 +238,8 @@ def cpu_baseline(w):
             "ms_per_product": dt / nprod * 1e3, "ms_per_iteration": dt / iters * 1e3,
             "single_core": {"value": 3 * 2.0 * a.nnz / dt1 / 1e9, "unit": "GFLOP/s",
                             "ms_per_product": dt1 / 3 * 1e3},
-            "cpu": _cpu_model()}
+            "cpu": _cpu_model(),
+            **({"cgls2d_128": _cgls2d_vs_oracle(c1)} if c1 else {})}
 
 
 def _cpu_model() -> str:
@@ -238,6 +261,174 @@ def _cpu_model() -> str:
     except OSError:
         pass
     return f"{name or platform.machine()}, {os.cpu_count()} logical cores"
+
+
+ROOF_KINDS = {0: "gather16_mixed_fma", 1: "mixed_fma", 2: "fp32_fma", 3: "gather16", 4: "gather16_fp32x2_fma"}
+
+
+def _measure_roof(stream, iters=20000, ctas_per_sm=2):
+    """The product kernel's core roofs measured on this GPU by the library's
+    roof probe (xct_roof_probe): rates of the product's inner step -- a
+    16-byte shared-memory gather by 8 lanes of one 128-byte row, feeding 8
+    mixed-precision FMAs -- and of its parts.  Returns per kind: operations
+    per second (FMAs, or 16-byte loads for the gathers alone) and the
+    derived flop rate (2 per FMA)."""
+    import torch
+    from paper_2009_07226_gb300 import xct
+    out = {}
+    for kind, name in ROOF_KINDS.items():
+        xct.xct_roof_probe(kind, iters // 10, ctas_per_sm, stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ops = xct.xct_roof_probe(kind, iters, ctas_per_sm, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sec = e0.elapsed_time(e1) * 1e-3
+        rate = ops / sec
+        out[name] = {"ms": sec * 1e3, "ops_per_s": rate,
+                     **({"tflops": 2.0 * rate / 1e12} if kind != 3 else {"tb_per_s": 16.0 * rate / 1e12})}
+    return out
+
+
+def _accuracy(xct, plans, p64, w, first, count, volume, S, n, K, y, y64, err_vs_phantom, stream, dev):
+    """The accuracy target (relative reconstruction error vs FP64) measured
+    where it is well posed.
+
+    noiseless: consistent data, where CGLS converges: the sinogram is the
+    FP64 projection of the rasterised phantom with the FP64 matrix
+    (xct_project_f64); each form's relative distance to the phantom after
+    K iterations and to the FP64 iterate, and |err_form - err_FP64|.
+
+    noisy: on the measured (Poisson) sinogram CGLS semi-converges: the
+    distance to the phantom falls to a minimum and then grows as the solve
+    fits the noise.  Each form's phantom error at 5, 10, 20 and K
+    iterations and at its best iteration (binary16 and FP32 every
+    iteration, through checkpoint / resume one iteration at a time; FP64 at
+    those counts and at the FP32 form's best iteration)."""
+    import torch
+    from paper_2009_07226_gb300 import inputs
+    phantom = torch.tensor(w["images"], dtype=torch.float64, device=dev)
+    yc64 = p64.project_f64(phantom, stream=stream)
+    yc = yc64.float()
+    del phantom
+    xc = {}
+    for kind in ("f16", "f32"):
+        xc[kind] = torch.empty((S, n, n), dtype=torch.float32, device=dev)
+        xct.xct_cgls(plans[kind].handle, yc, xc[kind], S, K, 0, None, stream)
+    xc["f64"] = torch.empty((S, n, n), dtype=torch.float64, device=dev)
+    xct.xct_cgls_f64(p64.handle, yc64, xc["f64"], S, K, 0, None, stream)
+    e_c = {k: err_vs_phantom(v) for k, v in xc.items()}
+    noiseless = {
+        "iters": K, "phantom_rel_err": e_c,
+        "rel_err_vs_fp64_iterate": {k: float(torch.linalg.norm(xc[k].double() - xc["f64"]) /
+                                             torch.linalg.norm(xc["f64"])) for k in ("f16", "f32")},
+        "abs_diff_phantom_err_vs_fp64": {k: abs(e_c[k] - e_c["f64"]) for k in ("f16", "f32")},
+    }
+    del xc, yc, yc64
+
+    def curve(kind):
+        plan = plans[kind]
+        state = torch.empty(xct.xct_cgls_state_bytes(plan.handle, S), dtype=torch.uint8, device=dev)
+        x = torch.empty((S, n, n), dtype=torch.float32, device=dev)
+        errs = []
+        for k in range(1, K + 1):
+            fl = xct.XCT_CGLS_SAVE | xct.XCT_CGLS_NO_GRAPH | (xct.XCT_CGLS_RESUME if k > 1 else 0)
+            xct.xct_cgls_state(plan.handle, y if k == 1 else None, x, S, 1, fl, state, None, stream)
+            errs.append(err_vs_phantom(x))
+        return errs
+
+    marks = sorted({5, 10, 20, K})
+    noisy = {"phantom_rel_err_by_iteration": {}, "best": {}}
+    curves = {k: curve(k) for k in ("f16", "f32")}
+    for kind, c in curves.items():
+        kb = int(np.argmin(c)) + 1
+        noisy["phantom_rel_err_by_iteration"][kind] = {k: c[k - 1] for k in marks}
+        noisy["best"][kind] = {"iteration": kb, "phantom_rel_err": c[kb - 1]}
+    kb32 = noisy["best"]["f32"]["iteration"]
+    e64 = {}
+    for k in sorted(set(marks) | {kb32}):
+        x64k = torch.empty((S, n, n), dtype=torch.float64, device=dev)
+        xct.xct_cgls_f64(p64.handle, y64, x64k, S, k, 0, None, stream)
+        e64[k] = err_vs_phantom(x64k)
+    noisy["phantom_rel_err_by_iteration"]["f64"] = {k: e64[k] for k in marks}
+    kb64 = min(e64, key=e64.get)
+    noisy["best"]["f64"] = {"iteration": kb64, "phantom_rel_err": e64[kb64],
+                            "note": "FP64 evaluated at 5, 10, 20, K and the FP32 best iteration"}
+    noisy["best_abs_diff_vs_fp64"] = {k: abs(noisy["best"][k]["phantom_rel_err"] - e64[kb64])
+                                      for k in ("f16", "f32")}
+    return {"noiseless": noiseless, "noisy": noisy}
+
+
+def _measure_cgls2d(steps):
+    """The plain 2D workload: one 128^2 slice, 180 angles, 128 bins, 10
+    random ellipses, noiseless sinogram (the rasterised phantom projected
+    with the FP64 matrix, xct_project_f64), 30 CGLS iterations from zero;
+    FP32 (the configuration's form) and binary16.
+    A (28 MB in FP32) and every vector fit in the 129 MB L2, so the byte
+    rate is reported against L2-resident data, not HBM."""
+    import torch
+    from paper_2009_07226_gb300 import inputs, xct
+    w = inputs.make_workload("cgls2d_128")
+    n, m, nd, S, K = w["n"], w["m"], w["nd"], w["slices"], w["iters"]
+    stream = torch.cuda.current_stream()
+    with xct.Plan(n, m, nd, "f32", cos_sin=w["cos_sin"], keep_f64=True) as p64:
+        y = p64.project_f64(torch.tensor(w["images"], dtype=torch.float64, device="cuda")).float()
+    out = {"n": n, "angles": m, "bins": nd, "slices": S, "iters": K, "l2_resident": True}
+    xs = {}
+    for kind in ("f32", "f16"):
+        with xct.Plan(n, m, nd, kind, cos_sin=w["cos_sin"]) as p:
+            st = p.stats()
+            x = torch.empty((S, n, n), device="cuda")
+            for _ in range(3):
+                xct.xct_cgls(p.handle, y, x, S, K, 0, None, stream)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                xct.xct_cgls(p.handle, y, x, S, K, 0, None, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            nnz = st["nnz"]
+            ebytes = 8 if kind == "f32" else 4
+            alg = nnz * ebytes + (m * nd + n * n + 2) * 8 + S * (m * nd + n * n) * 8
+            out[kind] = {"ms_per_solve": ms, "cgls_iter_per_s": K / (ms * 1e-3),
+                         "gflops": (2 * K + 1) * 2.0 * nnz * S / (ms * 1e-3) / 1e9,
+                         "alg_gbs": (2 * K + 1) * alg / (ms * 1e-3) / 1e9, "nnz": nnz}
+            xs[kind] = x.cpu().numpy().reshape(S, -1).astype(np.float64)
+    out["note"] = ("whole solves (graph path) including one natural <-> internal conversion; "
+                   "error against the FP64 oracle's solve is in cpu_baseline.cgls2d_128")
+    return out, xs, w
+
+
+def _workloads(args):
+    """The other configurations, each measured once in this process with
+    reduced repetition (stated per entry); their full-length runs are the
+    --mode batch / tv / large lines."""
+    import torch
+    res = {}
+    c1 = None
+    jobs = (("cgls2d_128", lambda: _measure_cgls2d(10)),
+            ("large3d_1536", lambda: _measure_large(2, 1)),
+            ("tv3d_1024", lambda: _measure_tv(1, with_autograd=False)),
+            ("batch_uneven_64", lambda: _measure_batch(1, 1, combos=("batched_mixed", "per_job_fp32"))))
+    reps = {"cgls2d_128": "3 warm-up + 10 timed solves", "large3d_1536": "1 warm-up + 2 timed solves per form",
+            "tv3d_1024": "1 warm-up + 1 timed 200-step run (native loop)",
+            "batch_uneven_64": "1 warm-up + 1 timed batch per form"}
+    for name, fn in jobs:
+        t0 = time.perf_counter()
+        try:
+            r = fn()
+            if name == "cgls2d_128":
+                r, xs, w1 = r
+                c1 = (xs, w1)
+            res[name] = {**r, "repetition": reps[name], "wall_s": time.perf_counter() - t0}
+        except Exception as e:      # keep the line: record the failure
+            res[name] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    return res, c1
 
 
 def run_ours(args):
@@ -398,6 +589,8 @@ def run_ours(args):
     vs64["rel_err_by_iteration"]["f16"][K] = vs64["f16"]["rel_err"]
     vs64["rel_err_by_iteration"]["f32"][K] = vs64["f32"]["rel_err"]
     del x64p
+    accuracy = _accuracy(xct, plans, p64, w, first, count, per_rank * world, S, n, K, y, y64,
+                         err_vs_phantom, stream, dev)
 
     if rank != 0:
         return
@@ -415,8 +608,12 @@ def run_ours(args):
     #    reads 2 bytes of a staged row from shared memory (128 B/clk/SM):
     #    both give nsm x 64 FMA/clk x 2 flop
     #  HBM: 2 flop per matrix entry and slice over the algorithmic bytes
-    fma_peak = 128 * 2 * nsm * clk / 1e12
-    op16_peak = 64 * 2 * nsm * clk / 1e12
+    fma_peak_derived = 128 * 2 * nsm * clk / 1e12
+    op16_peak_derived = 64 * 2 * nsm * clk / 1e12
+    # the same two roofs measured on this GPU (the library's roof probe)
+    roof = _measure_roof(stream)
+    fma_peak = roof["fp32_fma"]["tflops"]
+    op16_peak = roof["gather16_mixed_fma"]["tflops"]
     rows_a, cols_a = m * nd, n * n
     alg_bytes = nnz * 4 + (rows_a + 1) * 8 + S * cols_a * 2 + S * rows_a * 4
     alg_bytes_bp = nnz * 4 + (cols_a + 1) * 8 + S * rows_a * 2 + S * cols_a * 4
@@ -454,6 +651,7 @@ def run_ours(args):
                  "note": "one solve, kept FP64 CSR, FP64 FMAs (nominal GB300 FP64 rate 1.25 TFLOP/s); "
                          "FP32 and binary16 forms use the FP32-rounded sinogram"},
         "vs_fp64": vs64,
+        "accuracy_vs_fp64": accuracy,
         "rel_err_projection_vs_fp64": proj_err64,
         "graph_ms_per_step": graph_ms,
         "other_f16_ms_per_step": timed.parts["f16"],
@@ -463,12 +661,16 @@ def run_ours(args):
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "kernel": "spmm_pipe_kernel<__half,64> (projection, 2*nnz*S flops per launch)",
-            "peak_source": (f"derived, the least of three roofs at the median SM clock {sm_mhz:.0f} MHz: "
-                            f"16-bit operand roof {op16_peak:.1f} (one conversion per FMA issued beside "
-                            f"it, {nsm} SMs x 64 FMA/clk x 2 flop; equal to the shared-memory gather "
-                            f"roof at 2 B per FMA), FP32 FMA roof {fma_peak:.1f} ({nsm} x 128 FMA/clk x "
-                            f"2 flop), HBM roof {hbm_roof:.1f} (2*nnz*S flop over the algorithmic bytes "
+            "peak_source": (f"measured, the least of three roofs: the product's inner step (16-byte "
+                            f"shared-memory gather of one 128-byte staged row by 8 lanes feeding 8 "
+                            f"mixed-precision FMAs) {op16_peak:.1f} and FP32 FMAs {fma_peak:.1f}, both "
+                            f"timed by the library's roof probe on this GPU (derived at {sm_mhz:.0f} MHz: "
+                            f"{op16_peak_derived:.1f} for 64 FMA/clk/SM, {fma_peak_derived:.1f} for 128), "
+                            f"and the HBM roof {hbm_roof:.1f} (2*nnz*S flop over the algorithmic bytes "
                             f"at the measured {peak_hbm:.0f} GB/s)"),
+            "roof_probe": {k: {**v, "fma_per_clk_per_sm": (v["ops_per_s"] / (nsm * clk)
+                                                           if "tflops" in v else None)}
+                           for k, v in roof.items()},
             "fp32_fma": {"peak": fma_peak, "frac": achieved / fma_peak},
             "hbm": {"achieved_gbs": alg_bytes / (proj16 * 1e-3) / 1e9, "peak_gbs": peak_hbm,
                     "frac": alg_bytes / (proj16 * 1e-3) / 1e9 / peak_hbm, "peak_source": peak_kind,
@@ -483,9 +685,36 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(S * m * nd * 4), "d2h_bytes_per_step": int(S * n * n * 4)},
         "plan_ms": {"f16": st16["plan_ms"], "f32": plans["f32"].stats()["plan_ms"]},
     }
+    c1 = None
+    if world == 1 and not args.no_workloads:
+        for pl in plans.values():
+            pl.close()
+        del xs, logs, q16, q32
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        out["workloads"], c1 = _workloads(args)
     if not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w)
+        out["cpu_baseline"] = cpu_baseline(w, c1)
     print(json.dumps(out))
+
+
+def run_roof(args):
+    """The roof probe alone: the product kernel's core roofs on this GPU."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    sampler = ClockSampler(0)
+    sampler.start()
+    res = {c: _measure_roof(torch.cuda.current_stream(), iters=args.steps * 4000, ctas_per_sm=c)
+           for c in (1, 2, 3)}
+    clocks = sampler.stop()
+    clk = (clocks.get("sm_mhz") or 2070.0) * 1e6
+    for c, r in res.items():
+        for v in r.values():
+            v["per_clk_per_sm"] = v["ops_per_s"] / (nsm * clk)
+    print(json.dumps({"mode": "roof", "sms": nsm, "ctas_per_sm": res, "clocks": clocks}))
 
 
 def run_products(args):
@@ -594,7 +823,7 @@ def _job_sinos(jobs):
         return list(ex.map(inputs.job_sinograms, jobs))
 
 
-def run_batch(args):
+def _measure_batch(steps, warmup, combos=None):
     """The uneven batch: 64 seeded jobs, N in {256, 384, 512, 768}, M = 1.5 N,
     S ~ U{1..32}, 20 CGLS iterations each.  Mixed precision (binary16) in one
     batched, graph-captured, autotuned call per step, against per-job FP32
@@ -628,41 +857,51 @@ def run_batch(args):
             xct.xct_cgls(plans[(j["n"], kind)].handle, ys[i], xs[kind][i], j["slices"], K, 0, None, stream)
 
     def timed(fn, kind):
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             fn(kind)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0 = xct.xct_launch_count()
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             fn(kind)
         e1.record(stream)
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / args.steps, (xct.xct_launch_count() - l0) // args.steps
+        return e0.elapsed_time(e1) / steps, (xct.xct_launch_count() - l0) // steps
 
-    sampler = ClockSampler(0)
-    sampler.start()
     res = {}
-    for name, fn, kind in (("batched_mixed", batched, "f16"), ("per_job_fp32", per_job, "f32"),
-                           ("per_job_mixed", per_job, "f16"), ("batched_fp32", batched, "f32")):
+    all_combos = (("batched_mixed", batched, "f16"), ("per_job_fp32", per_job, "f32"),
+                  ("per_job_mixed", per_job, "f16"), ("batched_fp32", batched, "f32"))
+    for name, fn, kind in all_combos:
+        if combos and name not in combos:
+            continue
         ms, launches = timed(fn, kind)
         res[name] = {"ms_per_step": ms, "gflops": flops / (ms * 1e-3) / 1e9, "gpu_launches": launches}
-    clocks = sampler.stop()
     batched("f16")
     per_job("f32")
     torch.cuda.synchronize()
     rel = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(xs["f16"], xs["f32"]))
-    print(json.dumps({
-        "mode": "batch", "metric": "proj+backproj GFLOP/s of the uneven batch (2*nnz*S per product)",
+    for p in plans.values():
+        p.close()
+    return {
+        "metric": "proj+backproj GFLOP/s of the uneven batch (2*nnz*S per product)",
         "jobs": len(jobs), "slices": sum(j["slices"] for j in jobs), "iters": K,
         "slices_per_size": {n: sum(j["slices"] for j in jobs if j["n"] == n) for n in sizes},
         "nnz": nnz, "flops_per_step": flops, **res,
         "speedup_batched_mixed_vs_per_job_fp32": res["per_job_fp32"]["ms_per_step"] /
                                                   res["batched_mixed"]["ms_per_step"],
-        "max_rel_diff_mixed_vs_fp32": rel, "clocks": clocks}))
+        "max_rel_diff_mixed_vs_fp32": rel}
 
 
-def run_tv(args):
+def run_batch(args):
+    sampler = ClockSampler(0)
+    sampler.start()
+    out = _measure_batch(args.steps, args.warmup)
+    clocks = sampler.stop()
+    print(json.dumps({"mode": "batch", **out, "clocks": clocks}))
+
+
+def _measure_tv(reps, with_autograd=True):
     """The regularised reconstruction: 1024^2 grid, 720 angles, 1024 bins,
     16 slices, BF16 storage, 200 Adam steps on 0.5 ||A x - y||^2 +
     1e-3 TV_eps (eps 1e-3, lr 1e-2), through the fused native loop and
@@ -690,32 +929,38 @@ def run_tv(args):
         ag.tv_reconstruct(plan, y, steps=steps, lr=lr, lam=lam, eps=eps)
 
     res = {}
-    sampler = ClockSampler(0)
-    sampler.start()
-    for name, fn, reps in (("native", native, args.steps), ("autograd", autograd_loop, 1)):
+    runs = [("native", native, reps)] + ([("autograd", autograd_loop, 1)] if with_autograd else [])
+    for name, fn, r in runs:
         fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l0 = xct.xct_launch_count()
         e0.record(stream)
-        for _ in range(reps):
+        for _ in range(r):
             fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
+        ms = e0.elapsed_time(e1) / r
         res[name] = {"ms_per_run": ms, "ms_per_adam_step": ms / steps,
                      "gflops": steps * 2 * 2.0 * nnz * S / (ms * 1e-3) / 1e9,
-                     "gpu_launches_per_run": (xct.xct_launch_count() - l0) // reps}
-    clocks = sampler.stop()
+                     "gpu_launches_per_run": (xct.xct_launch_count() - l0) // r}
     native()
     lh = loss.cpu().numpy()
-    print(json.dumps({"mode": "tv", "metric": "Adam steps/s and product GFLOP/s (2 products of "
-                      "2*nnz*S flops per step)", "n": n, "angles": m, "bins": nd, "slices": S,
-                      "steps": steps, "storage": "bf16", "nnz": nnz, **res,
-                      "cost_first": float(lh[0]), "cost_last": float(lh[-1]), "clocks": clocks}))
+    plan.close()
+    return {"metric": "Adam steps/s and product GFLOP/s (2 products of 2*nnz*S flops per step)",
+            "n": n, "angles": m, "bins": nd, "slices": S, "steps": steps, "storage": "bf16",
+            "nnz": nnz, **res, "cost_first": float(lh[0]), "cost_last": float(lh[-1])}
 
 
-def run_large(args):
+def run_tv(args):
+    sampler = ClockSampler(0)
+    sampler.start()
+    out = _measure_tv(args.steps)
+    clocks = sampler.stop()
+    print(json.dumps({"mode": "tv", **out, "clocks": clocks}))
+
+
+def _measure_large(steps, warmup):
     """The large geometry: 1536^2 grid, 1024 angles, 1536 bins (A with about
     2.9e9 entries), 32 slices, 30 CGLS iterations, binary16 storage against
     FP32."""
@@ -737,38 +982,44 @@ def run_large(args):
     stream = torch.cuda.current_stream()
     y = torch.tensor(sino, dtype=torch.float32, device="cuda")
     res = {}
-    sampler = ClockSampler(0)
-    sampler.start()
     xs = {}
     for kind in ("f16", "f32"):
         plan = xct.Plan(n, m, nd, kind, cos_sin=inputs.angle_table(m))
         st = plan.stats()
         x = torch.empty((S, n, n), device="cuda")
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             xct.xct_cgls(plan.handle, y, x, S, K, xct.XCT_CGLS_TIMING, None, stream)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         tp = tb = 0.0
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             xct.xct_cgls(plan.handle, y, x, S, K, xct.XCT_CGLS_TIMING, None, stream)
             ps = plan.stats()
             tp += ps["t_project_ms"] / max(ps["n_project"], 1)
             tb += ps["t_backproject_ms"] / max(ps["n_backproject"], 1)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
+        ms = e0.elapsed_time(e1) / steps
         flops = (2 * K + 1) * 2.0 * st["nnz"] * S
         res[kind] = {"ms_per_solve": ms, "gflops": flops / (ms * 1e-3) / 1e9,
-                     "project_ms": tp / args.steps, "backproject_ms": tb / args.steps,
+                     "project_ms": tp / steps, "backproject_ms": tb / steps,
                      "plan_ms": st["plan_ms"], "bytes_a": st["bytes_a"], "bytes_at": st["bytes_at"]}
         xs[kind] = x
         plan.close()
-    clocks = sampler.stop()
+        torch.cuda.empty_cache()
     rel = float(torch.linalg.norm(xs["f16"] - xs["f32"]) / torch.linalg.norm(xs["f32"]))
-    print(json.dumps({"mode": "large", "n": n, "angles": m, "bins": nd, "slices": S, "iters": K,
-                      "nnz": st["nnz"], **res, "speedup_mixed_vs_fp32": res["f32"]["ms_per_solve"] /
-                      res["f16"]["ms_per_solve"], "rel_diff_mixed_vs_fp32": rel, "clocks": clocks}))
+    return {"n": n, "angles": m, "bins": nd, "slices": S, "iters": K,
+            "nnz": st["nnz"], **res, "speedup_mixed_vs_fp32": res["f32"]["ms_per_solve"] /
+            res["f16"]["ms_per_solve"], "rel_diff_mixed_vs_fp32": rel}
+
+
+def run_large(args):
+    sampler = ClockSampler(0)
+    sampler.start()
+    out = _measure_large(args.steps, args.warmup)
+    clocks = sampler.stop()
+    print(json.dumps({"mode": "large", **out, "clocks": clocks}))
 
 
 def run_cusparse(args):
@@ -907,14 +1158,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the other configurations' compact measurements in the default line")
     ap.add_argument("--mode", default="cgls", choices=["cgls", "products", "batch", "tv", "large", "cusparse", "matfree",
-                             "pipeline"])
+                             "pipeline", "roof"])
     ap.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16", "f16a", "bf16a"])
     ap.add_argument("--slices", type=int, default=0,
                     help="--mode products: slices per product (default: the workload's 64)")
     args = ap.parse_args()
     if args.mode == "products":
         run_products(args)
+    elif args.mode == "roof":
+        run_roof(args)
     elif args.mode == "batch":
         run_batch(args)
     elif args.mode == "tv":

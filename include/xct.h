@@ -266,6 +266,17 @@ xct_status xct_tv_reconstruct(xct_plan_t plan, const float* y, float* x, int32_t
                               int32_t steps, double lr, double lam, double eps, uint32_t flags,
                               double* loss, void* stream);
 
+/*
+ * xct_datafit -- the data term of Eq. 1 and its residual: r = q - y and
+ * value = sum over slices of 0.5 ||r_s||^2 (FP64, summed in a fixed order),
+ * for q = A x computed by xct_project; the gradient of the data term is then
+ * xct_backproject(r).  q, y, r: device float32 [S][len], r not overlapping q or y;
+ * value: NULL, or a host (the call is then synchronous) or device double.
+ * XCT_ERR_INVALID for host vectors or negative sizes.
+ */
+xct_status xct_datafit(const float* q, const float* y, float* r, int64_t len, int32_t S,
+                       double* value, void* stream);
+
 /* One job of a batched solve. */
 typedef struct {
   xct_plan_t plan;   /* the job's geometry */
@@ -379,6 +390,25 @@ xct_status xct_set_allocator(xct_alloc_fn alloc, xct_free_fn release, void* ctx)
  */
 xct_status xct_project_noalloc(xct_plan_t plan, const float* x, float* y, int32_t S,
                                void* stream);
+
+/*
+ * xct_roof_probe -- measures the core roofs of the product kernels on the
+ * current GPU (Sec. III-B's register and input reuse bound the product by
+ * the FMA and shared-memory rates once the matrix stream is not the limit).
+ * Launches ctas_per_sm (1..4) CTAs of 512 threads per SM on `stream`; every
+ * thread runs `iters` steps of 4 repetitions of the product's inner step.
+ * kind 0: a 16-byte shared-memory gather (8 lanes reading one 128-byte row at
+ * a pseudo-random index) feeding 8 mixed-precision FMAs (fma.rn.f32.f16);
+ * 1: the 8 mixed FMAs alone; 2: 8 FP32 FMAs alone; 3: the gathers alone;
+ * 4: the gather feeding 4 FP32 slices through packed FP32 FMAs.  *ops
+ * (host) receives the operation count of the launch: FMAs (kinds 0-2, 4) or
+ * 16-byte loads (kind 3); the caller times the launch (CUDA events on
+ * `stream`).  Asynchronous.  XCT_ERR_INVALID for kind outside 0..4, iters
+ * outside [1, 2^40], ctas_per_sm outside 1..4 or ops == NULL.  The paper has
+ * no counterpart (a measurement of this GPU).
+ */
+xct_status xct_roof_probe(int32_t kind, int64_t iters, int32_t ctas_per_sm, double* ops,
+                          void* stream);
 
 /* Thread-local message of the last failing call on this thread. */
 const char* xct_last_error(void);

@@ -16,7 +16,8 @@ What it computes, each step following the paper:
   sharing A (Sec. II-B: every ray u_{*,j} traces the same voxels in all
   slices; Sec. III-B2: the fused product A X = B).
 * ``project_rays`` / ``backproject_pixels`` -- the same products,
-  matrix-free, for a sample of rows (large grids).
+  matrix-free, for a sample of rows (large grids); ``backproject_rays`` --
+  the full back projection, matrix-free, as the scatter of every ray.
 * ``cgls``            -- least squares on A x = y (Eq. 1 with R = 0 and no
   constraint), in the CGLS form whose K iterations cost K projections and
   K + 1 back projections (Table IV footnote: 30 projections, 31 back
@@ -79,6 +80,8 @@ def _load():
         lib.orc_backproject_pixels.argtypes = [ci, ci, ci, f64p, cd, cd, cd, ci, f64p,
                                                i64p, c64, f64p]
         lib.orc_backproject_pixels.restype = ci
+        lib.orc_backproject_rays.argtypes = [ci, ci, ci, f64p, cd, cd, cd, ci, f64p, f64p]
+        lib.orc_backproject_rays.restype = ci
         lib.orc_trace_one.argtypes = [ci, cd, cd, cd, cd, i32p, f64p]
         lib.orc_trace_one.restype = ci
         lib.orc_set_threads.argtypes = [ci]
@@ -253,6 +256,24 @@ def backproject_pixels(g: Geometry, Y: np.ndarray, pixels) -> np.ndarray:
                                       g.det_spacing, g.det_offset, g.min_seg, S, Y,
                                       pixels, pixels.size, X):
             raise MemoryError
+    return X
+
+
+def backproject_rays(g: Geometry, Y: np.ndarray) -> np.ndarray:
+    """Matrix-free back projection X = A^T Y over all rays: every ray traced
+    again and its segment lengths scattered, x[pixel] += length * y[ray]
+    (the transpose product by its definition, for grids whose A does not
+    fit in host memory)."""
+    lib = _load()
+    Y = np.ascontiguousarray(Y, dtype=np.float64).reshape(-1, g.nrays)
+    S = Y.shape[0]
+    X = np.empty((S, g.npix), dtype=np.float64)
+    if S and g.nrays:
+        if lib.orc_backproject_rays(g.n, g.m, g.nd, g.table().reshape(-1), g.det_spacing,
+                                    g.det_offset, g.min_seg, S, Y, X):
+            raise MemoryError
+    elif S:
+        X[:] = 0.0
     return X
 
 

@@ -331,6 +331,54 @@ int orc_backproject_pixels(int n, int m, int nd, const double* cs,
 }
 
 /* One traced row, for tests: returns the count, fills col/val (ascending). */
+/* x = A^T y over all rays, matrix-free (the transpose product written as
+ * the scatter of each ray's segments: x[pixel] += length * y[ray]).  Each
+ * thread traces a fixed contiguous range of rays into its own buffer; the
+ * buffers are summed in thread order.  Returns nonzero on allocation
+ * failure. */
+int orc_backproject_rays(int n, int m, int nd, const double* cs, double dspace,
+                         double doff, double min_seg, int nslice, const double* Y,
+                         double* X) {
+  const int64_t npix = (int64_t)n * n, nray = (int64_t)m * nd;
+  const int nt = omp_get_max_threads();
+  double* part = (double*)calloc((size_t)nt * nslice * npix, sizeof(double));
+  if (!part) return 1;
+  int fail = 0;
+#pragma omp parallel num_threads(nt) reduction(| : fail)
+  {
+    const int t = omp_get_thread_num(), tn = omp_get_num_threads();
+    double* alpha = (double*)malloc(sizeof(double) * (size_t)(2 * n + 4));
+    entry_t* ent = (entry_t*)malloc(sizeof(entry_t) * (size_t)(2 * n + 4));
+    double* xt = part + (int64_t)t * nslice * npix;
+    if (!alpha || !ent) {
+      fail = 1;
+    } else {
+      const int64_t r0 = nray * t / tn, r1 = nray * (t + 1) / tn;
+      for (int64_t r = r0; r < r1; ++r) {
+        int k = (int)(r / nd), j = (int)(r % nd);
+        int c = trace_ray(n, cs[2 * k], cs[2 * k + 1],
+                          ray_offset(j, nd, dspace, doff), min_seg, alpha, ent);
+        for (int s = 0; s < nslice; ++s) {
+          const double yv = Y[(int64_t)s * nray + r];
+          for (int e = 0; e < c; ++e) xt[(int64_t)s * npix + ent[e].col] += ent[e].val * yv;
+        }
+      }
+    }
+    free(alpha);
+    free(ent);
+  }
+  if (!fail) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < (int64_t)nslice * npix; ++i) {
+      double acc = 0.0;
+      for (int t = 0; t < nt; ++t) acc += part[(int64_t)t * nslice * npix + i];
+      X[i] = acc;
+    }
+  }
+  free(part);
+  return fail;
+}
+
 int orc_trace_one(int n, double c, double s, double t, double min_seg,
                   int32_t* col, double* val) {
   double* alpha = (double*)malloc(sizeof(double) * (size_t)(2 * n + 4));

@@ -112,3 +112,40 @@ extern "C" xct_status xct_tv_reconstruct(xct_plan_t plan, const float* y, float*
   }
   return XCT_OK;
 }
+
+extern "C" xct_status xct_datafit(const float* q, const float* y, float* r, int64_t len,
+                                  int32_t S, double* value, void* stream) {
+  Trace trace_("xct_datafit");
+  if (S < 0 || len < 0 || ((!q || !y || !r) && (int64_t)S * len > 0)) {
+    set_error("xct_datafit: bad arguments (S = %d, len = %lld)", S, (long long)len);
+    return XCT_ERR_INVALID;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool vh = value && on_host(value);
+  if ((int64_t)S * len == 0) {
+    if (value) {
+      if (vh) *value = 0.0;
+      else XCT_TRY_CUDA(cudaMemsetAsync(value, 0, sizeof(double), s));
+    }
+    return XCT_OK;
+  }
+  if (on_host(q) || on_host(y) || on_host(r)) {
+    set_error("xct_datafit takes device vectors");
+    return XCT_ERR_INVALID;
+  }
+  Arena ar(s);
+  double *rpart, *zero, *val;
+  XCT_TRY(ar.get(&rpart, (size_t)S * kVecBlocks));
+  XCT_TRY(ar.get(&zero, (size_t)S));
+  XCT_TRY(ar.get(&val, 1));
+  XCT_TRY_CUDA(cudaMemsetAsync(zero, 0, sizeof(double) * S, s));
+  // one slice per tile: r = q - y and the per-slice partials of ||r||^2,
+  // then sum_s 0.5 ||r_s||^2 in a fixed order
+  XCT_TRY(vec_sub_sumsq(q, y, r, len, 1, S, nullptr, rpart, s));
+  XCT_TRY(vec_loss(rpart, zero, S, value && !vh ? value : val, s));
+  if (vh) {
+    XCT_TRY_CUDA(cudaMemcpyAsync(value, val, sizeof(double), cudaMemcpyDeviceToHost, s));
+    XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  }
+  return XCT_OK;
+}

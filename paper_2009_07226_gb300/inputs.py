@@ -179,12 +179,15 @@ def gaussian_noise(rng: np.random.Generator, sino: np.ndarray, frac: float) -> n
 # ---------------------------------------------------------------------------
 
 def make_workload(name: str, slices: int | None = None, slice_offset: int = 0,
-                  with_images: bool = True, volume_slices: int | None = None):
+                  with_images: bool = True, volume_slices: int | None = None,
+                  noiseless: bool = False):
     """Phantom volume [S, n, n] (or None) and measured sinograms [S, m, nd]
     (float64) for one of WORKLOADS, seeded by the workload's seed.  Slices
     [slice_offset, slice_offset + slices) of a volume of `volume_slices`
     slices (default: the workload's slice count) are produced, so ranks
-    sharing a volume get disjoint slice ranges of the same phantom."""
+    sharing a volume get disjoint slice ranges of the same phantom.  With
+    noiseless=True the sinograms are the exact line integrals (no noise
+    drawn)."""
     w = WORKLOADS[name]
     n, m, nd = w["n"], w["m"], w["nd"]
     total = w["slices"] if volume_slices is None else volume_slices
@@ -202,7 +205,7 @@ def make_workload(name: str, slices: int | None = None, slice_offset: int = 0,
     noise = w["noise"]
     for s in range(S):
         nrng = np.random.default_rng(1_000_000 * w["seed"] + slice_offset + s)
-        if noise is None:
+        if noise is None or noiseless:
             continue
         if noise[0] == "poisson":
             sino[s] = poisson_noise(nrng, sino[s], n, noise[1])

@@ -88,6 +88,8 @@ _SIGNATURES = [
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, ctypes.c_uint32,
                                           ctypes.c_void_p, ctypes.c_void_p]),
+    ("xct_datafit", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                   ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     ("xct_cgls_batch", ctypes.c_int, [ctypes.POINTER(xct_job), ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_uint32, ctypes.c_void_p]),
     ("xct_plan_stats", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(xct_stats)]),
@@ -121,6 +123,8 @@ _SIGNATURES = [
     ("xct_set_wait_limit", ctypes.c_int, [ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
     ("xct_plan_check", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     ("xct_version", ctypes.c_char_p, []),
+    ("xct_roof_probe", ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                      ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]),
 ]
 
 _lib = None
@@ -271,6 +275,10 @@ def xct_adam(x, g, m, v, count: int, lr: float, beta1: float, beta2: float, eps:
                           _stream(stream)))
 
 
+def xct_datafit(q, y, r, length: int, S: int, value=None, stream=None) -> None:
+    _check(lib().xct_datafit(_ptr(q), _ptr(y), _ptr(r), length, S, _ptr(value), _stream(stream)))
+
+
 def xct_tv_reconstruct(plan: int, y, x, S: int, steps: int, lr: float, lam: float, eps: float,
                        flags: int = 0, loss=None, stream=None) -> None:
     _check(lib().xct_tv_reconstruct(plan, _ptr(y), _ptr(x), S, steps, lr, lam, eps, flags,
@@ -363,6 +371,13 @@ def xct_plan_check(plan: int, stream=None) -> None:
     """Raise XctError(XCT_ERR_TIMEOUT) if a product of this plan gave up a
     wait since the last check."""
     _check(lib().xct_plan_check(plan, _stream(stream)))
+
+
+def xct_roof_probe(kind: int, iters: int, ctas_per_sm: int = 2, stream=None) -> float:
+    """Launch the roof probe (asynchronous); returns its operation count."""
+    ops = ctypes.c_double()
+    _check(lib().xct_roof_probe(kind, iters, ctas_per_sm, ctypes.byref(ops), _stream(stream)))
+    return ops.value
 
 
 def xct_version() -> str:

@@ -106,6 +106,33 @@ def test_cost_gradient_vs_oracle(xct, small):
     assert abs(float(loss.detach()) - want) <= 1e-5 * want
 
 
+def test_datafit_function_vs_oracle(xct, small):
+    """The data term through library calls only (projection, xct_datafit,
+    back projection): value 0.5 ||A x - y||^2 and gradient A^T (A x - y)
+    against the FP64 oracle, with an incoming gradient of 3."""
+    from paper_2009_07226_gb300 import autograd as ag
+    cs, a, at, x, y = small
+    x64, y64 = x.astype(np.float64), y.astype(np.float64)
+    r = oracle.project(a, x64) - y64
+    with xct.Plan(N, M, ND, "f32", cos_sin=cs) as p:
+        xt = torch.tensor(x.reshape(S, N, N), device="cuda", requires_grad=True)
+        yt = torch.tensor(y.reshape(S, M, ND), device="cuda")
+        val = ag.datafit(xt, yt, p)
+        (3.0 * val).backward()
+        # value also through a host pointer
+        q = p.project(xt.detach())
+        rr = torch.empty_like(q)
+        host = np.zeros(1)
+        xct.xct_datafit(q, yt, rr, M * ND, S, host)
+    want = 0.5 * float((r * r).sum())
+    assert abs(float(val) - want) <= 1e-5 * want
+    assert abs(host[0] - float(val)) == 0.0
+    np.testing.assert_allclose(rr.cpu().numpy().reshape(S, -1), r, rtol=0, atol=1e-5 * np.abs(r).max())
+    g = xt.grad.cpu().numpy().reshape(S, -1).astype(np.float64)
+    ref = 3.0 * oracle.backproject(at, r)
+    assert np.linalg.norm(g - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
 def test_native_reconstruction_matches_autograd_loop(xct, small):
     from paper_2009_07226_gb300 import autograd as ag
     cs, a, at, x, y = small

@@ -134,38 +134,48 @@ def test_cgls_host_buffers(xct, cgls2d):
     assert np.array_equal(rh, ld.cpu().numpy())
 
 
-@pytest.mark.parametrize("kind,tol,track", [("f16", 2e-3, 0.15), ("bf16", 1.5e-2, 0.25)])
-def test_mixed_cgls_stable_phase_and_tracking(xct, kind, tol, track):
-    """Batched noisy 3D slices (Poisson at 1e4 photons).  Over the stable
-    phase the mixed iterate is within the 16-bit envelope of the FP64
-    oracle's; over 20 iterations the mixed residual curve stays within 15%
-    (binary16) / 25% (bfloat16, 8x the unit roundoff) of FP32's at every
-    iteration -- a numpy model of the binary16 arithmetic departs by 4-10%
-    -- and the final residual within 3%."""
-    n, m, nd, S = 64, 96, 64, 8
-    cs = inputs.angle_table(m)
-    rng = np.random.default_rng(2)
-    ells = inputs.random_ellipsoids(rng, 20)
-    sino = np.stack([inputs.line_integrals(inputs.cut_ellipsoids(ells, inputs.slice_z(s, S)), n, cs, nd)
-                     for s in range(S)])
-    for s in range(S):
-        sino[s] = inputs.poisson_noise(np.random.default_rng(100 + s), sino[s], n, 1e4)
-    g = oracle.Geometry(n=n, m=m, nd=nd, cos_sin=cs)
-    a = oracle.siddon_csr(g)
-    at = oracle.transpose(a)
+@pytest.mark.parametrize("kind,tol_model", [("f16", 1e-4), ("bf16", 5e-4)])
+def test_mixed_cgls_stable_phase_and_tracking(xct, kind, tol_model):
+    """Batched noisy 3D slices (Poisson at 1e4 photons), against the
+    oracle's model of the mixed-precision solve (its CGLS over its
+    mixed-precision products, Sec. III-C; tests/_mixed_envelope.py).
+
+    Stable phase (k = 1, 3, 5): the GPU's mixed iterate equals the model's
+    within tol_model.  The two differ only by FP32 rounding (GPU sums and
+    vectors in FP32, the model's sums exact): keeping the model's vectors in
+    FP32 moves its k = 5 iterate by 2e-6 (binary16) / 1e-5 (bfloat16), and
+    the bounds leave a factor of 50 over that.  The GPU's distance to the FP64
+    solve is then the model's own, up to the same tolerance.
+
+    After the stable phase the trajectory is chaotic, so the residual curve
+    is held to the rounding envelope the oracle computes: over 20 iterations
+    the GPU's mixed ||r_k|| stays within 1.1x the envelope's worst deviation
+    from the FP32 solve (binary16 15.1%, bfloat16 24.9%, pinned by
+    test_oracle_cgls_sensitivity.py::test_mixed_envelope) and within 1.25x
+    its deviation at iteration 20 (2.1% / 3.3%).  The margins cover that the
+    GPU is one more sample of the rounding process: the samples' worst
+    deviations spread by about 30% (binary16: 11.6% .. 15.1%)."""
+    import _mixed_envelope as me
+    n, m, nd, S, cs, sino, a, at = me.noisy_batch()
+    b32 = me._to_f32(sino.reshape(S, -1))
     bt = torch.tensor(sino, dtype=torch.float32, device="cuda")
     with xct.Plan(n, m, nd, "f32", cos_sin=cs) as p32, xct.Plan(n, m, nd, kind, cos_sin=cs) as pm:
         for k in (1, 3, 5):
             xr, _ = oracle.cgls(*_ops(a, at), sino.reshape(S, -1), k)
+            xmod, _ = oracle.cgls(*me.mixed_ops(a, at, kind), b32, k)
             x32 = p32.cgls(bt, k).cpu().numpy().reshape(S, -1)
             xm = pm.cgls(bt, k).cpu().numpy().reshape(S, -1)
             assert np.linalg.norm(x32 - xr) / np.linalg.norm(xr) <= 2e-5
-            assert np.linalg.norm(xm - xr) / np.linalg.norm(xr) <= tol, (k, kind)
+            e_model = np.linalg.norm(xm - xmod) / np.linalg.norm(xmod)
+            assert e_model <= tol_model, (k, kind, e_model)
+            e64, e64_model = (np.linalg.norm(v - xr) / np.linalg.norm(xr) for v in (xm, xmod))
+            assert e64 <= e64_model + tol_model, (k, kind, e64, e64_model)
         _, l32 = p32.cgls(bt, 20, resid=True)
         _, lm = pm.cgls(bt, 20, resid=True)
-    ratio = lm.cpu().numpy()[:, :, 0] / l32.cpu().numpy()[:, :, 0]
-    assert np.max(np.abs(ratio - 1)) <= track
-    assert np.max(np.abs(ratio[-1] - 1)) <= 0.03
+    env = me.envelope(a, at, sino.reshape(S, -1), kind, 20)
+    dev = me.residual_deviation(lm.cpu().numpy(), l32.cpu().numpy())
+    assert dev.max() <= 1.1 * env["max"], (dev.max(), env)
+    assert dev[-1].max() <= 1.25 * env["final"], (dev[-1].max(), env)
 
 
 @pytest.mark.parametrize("kind,tol", [("f16a", 1e-3), ("bf16a", 8e-3)])

@@ -2,11 +2,15 @@
 state saved, then m iterations resumed from it, give the x and residual log
 of k + m uninterrupted iterations bit for bit -- from device or host state
 buffers, in FP32 and binary16 storage, with or without a CUDA graph; a state
-of another plan or slice count is rejected."""
+of another plan or slice count is rejected.  Over the stable phase (k + m
+<= 5 iterations) a resumed solve also equals the oracle's: the FP64 CGLS
+within 2e-5 (FP32 storage, the bar of the plain solver) and the oracle's
+model of the binary16 solve within 1e-4 (the bar of the mixed solver)."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2009_07226_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -22,15 +26,19 @@ def xct():
     return x
 
 
-@pytest.fixture(scope="module")
-def sino():
+def _sino_host():
     cs = inputs.angle_table(M)
     ells = inputs.random_ellipsoids(np.random.default_rng(9), 20)
     out = np.stack([inputs.line_integrals(inputs.cut_ellipsoids(ells, inputs.slice_z(s, S)), N, cs, ND)
                     for s in range(S)])
     for s in range(S):
         out[s] = inputs.poisson_noise(np.random.default_rng(300 + s), out[s], N, 1e4)
-    return torch.tensor(out, dtype=torch.float32, device="cuda")
+    return out.astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def sino():
+    return torch.tensor(_sino_host(), device="cuda")
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
@@ -80,3 +88,36 @@ def test_state_of_another_problem_is_rejected(xct, sino):
         with pytest.raises(xct.XctError) as e2:       # neither flag
             xct.xct_cgls_state(p.handle, sino, x, S, 2, 0, state)
         assert e2.value.status == xct.XCT_ERR_INVALID
+
+
+@pytest.mark.parametrize("storage,k,m", [("f32", 2, 3), ("f32", 4, 1), ("f16", 2, 3)])
+def test_resumed_stable_phase_equals_the_oracle(xct, sino, storage, k, m):
+    """k iterations saved, m resumed (k + m <= 5, the stable phase): the
+    iterate and the residual log against the oracle's solve of k + m
+    iterations on the same FP32 sinogram."""
+    import _mixed_envelope as me
+    b = _sino_host().reshape(S, -1).astype(np.float64)
+    g = oracle.Geometry(n=N, m=M, nd=ND, cos_sin=inputs.angle_table(M))
+    a = oracle.siddon_csr(g)
+    at = oracle.transpose(a)
+    if storage == "f32":
+        ops, tol = ((lambda X: oracle.project(a, X)), (lambda Y: oracle.backproject(at, Y))), 2e-5
+    else:
+        ops, tol = me.mixed_ops(a, at, storage), 1e-4
+    xr, lr = oracle.cgls(*ops, b, k + m)
+    with xct.Plan(N, M, ND, storage, cos_sin=inputs.angle_table(M)) as p:
+        state = torch.zeros(xct.xct_cgls_state_bytes(p.handle, S), dtype=torch.uint8, device="cuda")
+        x = torch.empty((S, N, N), device="cuda")
+        log1 = torch.zeros((k + 1, S, 2), dtype=torch.float64, device="cuda")
+        xct.xct_cgls_state(p.handle, sino, x, S, k, xct.XCT_CGLS_SAVE, state, log1)
+        log2 = torch.zeros((m + 1, S, 2), dtype=torch.float64, device="cuda")
+        xct.xct_cgls_state(p.handle, None, x, S, m, xct.XCT_CGLS_RESUME, state, log2)
+        torch.cuda.synchronize()
+    xg = x.cpu().numpy().reshape(S, -1)
+    assert np.linalg.norm(xg - xr) / np.linalg.norm(xr) <= tol
+    log = np.concatenate([log1.cpu().numpy(), log2.cpu().numpy()[1:]])
+    np.testing.assert_allclose(log[:, :, 0], lr[:, :, 0], rtol=tol)
+    # ||A^T r_k|| is the norm of A^T b - A^T A x_k: a relative error in
+    # either term is amplified by ||A^T b|| / ||A^T r_k||
+    amp = float(np.max(lr[0, :, 1] / lr[:, :, 1]))
+    np.testing.assert_allclose(log[:, :, 1], lr[:, :, 1], rtol=tol * amp)

@@ -85,3 +85,37 @@ def test_mixed_cgls_residual_of_two_slices(xct, geom):
     # recomputes it with the FP64 matrix
     assert np.all(np.abs(rk - true_r) <= 1e-2 * true_r), (rk, true_r)
     assert np.allclose(r0, np.linalg.norm(bb, axis=1), rtol=1e-6)
+
+
+@pytest.fixture(scope="module")
+def two_slices(geom):
+    """The FP64 oracle's CGLS of two slices, 3 iterations, matrix-free."""
+    w = inputs.make_workload("large3d_1536", with_images=False)
+    b = w["sino"].astype(np.float32)
+    pick = [S // 4, 3 * S // 4]
+    bp = b.reshape(S, -1)[pick].astype(np.float64)
+    xr, lr = oracle.cgls(lambda X: oracle.project_rays(geom, X),
+                         lambda Y: oracle.backproject_rays(geom, Y), bp, 3)
+    return w, b, pick, xr, lr
+
+
+@pytest.mark.parametrize("kind,tol", [("f32", 2e-5), ("f16", 2e-3)])
+def test_cgls_stable_phase_of_two_slices_vs_oracle(xct, two_slices, kind, tol):
+    """The 32-slice solve of the large workload against the FP64 oracle's
+    CGLS of two of its slices over the stable phase (3 iterations), the
+    oracle's products computed matrix-free (A of this size does not fit in
+    host memory): the iterate after 3 iterations and the residual log
+    (||r_k||, ||A^T r_k||, k = 0..3) within the stable-phase bars of the
+    plain solver (FP32: 2e-5; binary16: 2e-3, as on the 3D batch).  The
+    two slices cut the phantom through its middle (an end slice of the
+    volume may cut no ellipsoid)."""
+    w, b, pick, xr, lr = two_slices
+    with xct.Plan(N, M, ND, kind, cos_sin=w["cos_sin"]) as p:
+        xk, log = p.cgls(torch.tensor(b, device="cuda"), 3, resid=True)
+        torch.cuda.synchronize()
+        xs = xk.reshape(S, -1)[pick].double().cpu().numpy()
+        lg = log.cpu().numpy()[:, pick, :]
+        del xk
+    for s in range(2):
+        assert np.linalg.norm(xs[s] - xr[s]) / np.linalg.norm(xr[s]) <= tol, (kind, s)
+    np.testing.assert_allclose(lg, lr, rtol=tol)

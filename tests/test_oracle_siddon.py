@@ -239,6 +239,29 @@ def test_matrix_free_adjoint():
     np.testing.assert_allclose(oracle.backproject(at, y), aty, rtol=0, atol=1e-11)
 
 
+@pytest.mark.parametrize("n,m,nd,off,sp", [(8, 8, 8, 0.0, 1.0), (24, 19, 31, -0.37, 0.9),
+                                            (37, 23, 41, -0.4, 1.0), (8, 5, 4, 100.0, 1.0)])
+def test_ray_scatter_back_projection(n, m, nd, off, sp):
+    """The matrix-free back projection by rays (each ray's lengths scattered
+    into its pixels) equals the product with the explicit transpose, equals
+    the pixel-driven one, and is the adjoint of the ray-driven projection --
+    three independent traversals of A."""
+    g = _geom(n, m, nd, off, sp)
+    rng = np.random.default_rng(n + m)
+    x = rng.standard_normal((3, g.npix))
+    y = rng.standard_normal((3, g.nrays))
+    aty = oracle.backproject_rays(g, y)
+    at = oracle.transpose(oracle.siddon_csr(g))
+    np.testing.assert_allclose(aty, oracle.backproject(at, y), rtol=0, atol=1e-12 * max(1.0, np.abs(aty).max()))
+    np.testing.assert_allclose(aty, oracle.backproject_pixels(g, y, np.arange(g.npix)), rtol=0,
+                               atol=1e-11 * max(1.0, np.abs(aty).max()))
+    ax = oracle.project_rays(g, x)
+    lhs = np.einsum("ij,ij->i", ax, y)
+    rhs = np.einsum("ij,ij->i", x, aty)
+    scale = np.linalg.norm(ax, axis=1) * np.linalg.norm(y, axis=1) + 1e-300
+    assert np.all(np.abs(lhs - rhs) <= 1e-12 * scale)
+
+
 def test_empty_and_degenerate_geometries():
     # all rays miss the grid
     g = _geom(8, 5, 4, offset=100.0)
