@@ -376,8 +376,9 @@ xct_status xct_set_allocator(xct_alloc_fn alloc, xct_free_fn release, void* ctx)
  * a plan there (its address is looked up then, with the plan's device
  * current), or at the latest on the first xct_project_noalloc call on that
  * device, and stays until the process exits.  With st the slice tile the
- * library picks for S (1, 2, 4, ..., 64 for XCT_F16 / XCT_BF16, up to 32
- * otherwise, at least 8 for XCT_F16A / XCT_BF16A) and S_pad = st *
+ * library picks for S (the least power of two >= S within 8..64 for
+ * XCT_F16 / XCT_BF16, 4..32 for XCT_F32, 8..32 for XCT_F16A / XCT_BF16A)
+ * and S_pad = st *
  * ceil(S / st), a call needs, each term rounded up to a multiple of 256
  * bytes: 4 * S_pad * n*n (input) + 4 * S_pad * M*N_d (output) + 2 * S_pad *
  * n*n (XCT_F16 and XCT_BF16 only: the 16-bit copy) + 4 * S_pad (per-slice

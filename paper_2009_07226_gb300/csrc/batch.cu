@@ -64,8 +64,9 @@ xct_status choose_tile(Plan& p, int S, bool tune, cudaStream_t s, int* out) {
     *out = it->second;
     return XCT_OK;
   }
-  const std::vector<int> cand = stages16(p.storage) ? std::vector<int>{16, 32, 64}
-                                                     : std::vector<int>{8, 16, 32};
+  const std::vector<int> cand = stages16(p.storage) ? std::vector<int>{8, 16, 32, 64}
+                                                     : (matrix16(p.storage) ? std::vector<int>{8, 16, 32}
+                                                                            : std::vector<int>{4, 8, 16, 32});
   double best = 1e300;
   int best_st = pick_slices_per_tile(p.storage, S);
   for (int st : cand) {

@@ -774,29 +774,33 @@ __global__ void stage_ent_kernel(const int64_t* slot_off, int64_t nstages, int64
     atomicMax(emax, (unsigned long long)(slot_off[(s + 1) * kQuads] - slot_off[s * kQuads]));
 }
 
+// every slot starts as a padding entry: the zero slot (position `zero_slot`)
+// with value 0
 template <int EB>
 __global__ void pad_fill_kernel(void* ent, int64_t nslots, uint32_t zero_slot) {
+  const uint32_t off = zero_slot * (uint32_t)kEntryRowBytes;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nslots;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (EB == 4)
-      static_cast<uint32_t*>(ent)[i] = zero_slot;
+      static_cast<uint32_t*>(ent)[i] = off << 16;
     else
-      static_cast<unsigned long long*>(ent)[i] = zero_slot;
+      static_cast<unsigned long long*>(ent)[i] = off;
   }
 }
 
 template <int KIND>  // 0: f32, 1: f16 (x 2^15), 2: bf16
 __device__ __forceinline__ void pack_entry(void* ent, int64_t slot, uint32_t local, double v) {
+  const uint32_t off = local * (uint32_t)kEntryRowBytes;
   if (KIND == 0) {
-    unsigned long long w = (unsigned long long)local |
+    unsigned long long w = (unsigned long long)off |
                            ((unsigned long long)__float_as_uint(__double2float_rn(v)) << 32);
     static_cast<unsigned long long*>(ent)[slot] = w;
   } else if (KIND == 1) {
     unsigned short h = __half_as_ushort(__double2half(dmul(v, 32768.0)));
-    static_cast<uint32_t*>(ent)[slot] = (local & 0xffffu) | ((uint32_t)h << 16);
+    static_cast<uint32_t*>(ent)[slot] = (off << 16) | h;
   } else {
     unsigned short h = __bfloat16_as_ushort(__double2bfloat16(v));
-    static_cast<uint32_t*>(ent)[slot] = (local & 0xffffu) | ((uint32_t)h << 16);
+    static_cast<uint32_t*>(ent)[slot] = (off << 16) | h;
   }
 }
 
@@ -1342,10 +1346,11 @@ xct_status export_matrix(Plan& p, int what, int64_t* rowptr, int32_t* col, doubl
               int64_t slot = s.off + (k >> 2) * 16 + g * 4 + (k & 3);
               uint32_t idx;
               double v;
+              uint32_t off;
               if (L.ebytes == 4) {
                 uint32_t w = e4[slot];
-                idx = w & 0xffffu;
-                uint16_t h = (uint16_t)(w >> 16);
+                off = w >> 16;
+                uint16_t h = (uint16_t)(w & 0xffffu);
                 if (half_values(p.storage)) {
                   __half_raw hr;
                   hr.x = h;
@@ -1358,13 +1363,14 @@ xct_status export_matrix(Plan& p, int what, int64_t* rowptr, int32_t* col, doubl
                 }
               } else {
                 unsigned long long w = e8[slot];
-                idx = (uint32_t)(w & 0xffffffffu);
+                off = (uint32_t)(w & 0xffffffffu);
                 uint32_t f = (uint32_t)(w >> 32);
                 float ff;
                 memcpy(&ff, &f, 4);
                 v = ff;
               }
-              if (idx >= (uint32_t)(sp[st + 1] - sp[st]) || row >= nrows) {
+              idx = off / kEntryRowBytes;
+              if (off % kEntryRowBytes || idx >= (uint32_t)(sp[st + 1] - sp[st]) || row >= nrows) {
                 set_error("packed layout holds an out-of-range entry (block %d stage %lld)", b,
                           (long long)st);
                 return XCT_ERR_CUDA;

@@ -24,7 +24,7 @@ namespace {
 
 constexpr int kProbeThreads = 512;       // 16 warps, as the product's consumers
 constexpr int kProbeRows = 256;          // staged rows of 128 bytes (32 KB)
-__device__ float g_roof_sink;            // written only if a sum is negative (never)
+__device__ float g_roof_sink;            // keeps the probe's results live
 
 __device__ __forceinline__ void mixed8(float* acc, const uint4& v, unsigned short w) {
   const uint32_t* x = reinterpret_cast<const uint32_t*>(&v);
@@ -88,11 +88,12 @@ __global__ void __launch_bounds__(kProbeThreads, 2) roof_kernel(int64_t iters, u
       }
     }
   }
-  float s = (float)xo;
+  float s = __uint_as_float(xo & 0x007fffffu);
 #pragma unroll
   for (int i = 0; i < 8; ++i) s += acc[i];
-  // every operand is positive, so this never stores; it keeps the results live
-  if (s < 0.0f) g_roof_sink = s;
+  // a comparison with a launch argument keeps every result (and load) live;
+  // when it holds, the store is a harmless write of one scalar
+  if (s == __uint_as_float(seed)) g_roof_sink = s;
 }
 
 }  // namespace

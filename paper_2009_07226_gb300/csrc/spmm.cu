@@ -14,9 +14,10 @@
 //   * output buffering (Sec. III-B3): per-lane FP32 accumulators, written
 //     once, with the per-slice squared norm reduced in the epilogue (the CGLS
 //     dot product, FP64);
-//   * packing (Sec. III-C2): {u16 stage index, 16-bit value} entries (4 bytes)
-//     for mixed precision, {u32 index, f32 value} (8 bytes) for FP32; four
-//     entries per 16-byte vector load, broadcast to the lanes of a group;
+//   * packing (Sec. III-C2): {16-bit value, u16 staged-row byte offset}
+//     entries (4 bytes) for mixed precision, {u32 offset, f32 value} (8
+//     bytes) for FP32; four entries per 16-byte vector load, broadcast to the
+//     lanes of a group;
 //   * mixed precision (Sec. III-C): 16-bit values times 16-bit staged inputs
 //     accumulate in FP32 through the mixed-precision FMA (fma.rn.f32.f16 /
 //     .bf16, sm_100+); normalisation by 2^-e per slice during staging,
@@ -258,14 +259,18 @@ __global__ void __launch_bounds__(Cfg<TX, ST>::NT, Cfg<TX, ST>::MIN_BLOCKS)
 #pragma unroll
         for (int w = 0; w < CW; ++w) pf[PF - 1][w] = __ldg(ep + (c + PF) * 4 * CW + w);
       }
-      uint32_t idx[4], val[4];
+      // byte offsets of the staged rows (at 128 bytes per row in the entry,
+      // shifted to this tile's row size) and value bits
+      constexpr int OSH = entry_shift(C::PIXB);
+      uint32_t off[4], val[4];
       if constexpr (C::E16) {
         const uint32_t e4[4] = {cur[0].x, cur[0].y, cur[0].z, cur[0].w};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) { idx[q] = e4[q] & 0xffffu; val[q] = e4[q] >> 16; }
+        for (int q = 0; q < 4; ++q) { off[q] = e4[q] >> (16 + OSH); val[q] = e4[q] & 0xffffu; }
       } else {
-        idx[0] = cur[0].x; val[0] = cur[0].y; idx[1] = cur[0].z; val[1] = cur[0].w;
-        idx[2] = cur[CW - 1].x; val[2] = cur[CW - 1].y; idx[3] = cur[CW - 1].z; val[3] = cur[CW - 1].w;
+        off[0] = cur[0].x >> OSH; val[0] = cur[0].y; off[1] = cur[0].z >> OSH; val[1] = cur[0].w;
+        off[2] = cur[CW - 1].x >> OSH; val[2] = cur[CW - 1].y;
+        off[3] = cur[CW - 1].z >> OSH; val[3] = cur[CW - 1].w;
       }
       typename VecT<C::VB>::T xv[4][C::VPL];
 #pragma unroll
@@ -273,7 +278,7 @@ __global__ void __launch_bounds__(Cfg<TX, ST>::NT, Cfg<TX, ST>::MIN_BLOCKS)
 #pragma unroll
         for (int v = 0; v < C::VPL; ++v)
           xv[q][v] = *reinterpret_cast<const typename VecT<C::VB>::T*>(
-              sbase + (size_t)idx[q] * C::PIXB + v * C::LPR * C::VB);
+              sbase + off[q] + v * C::LPR * C::VB);
 #pragma unroll
       for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -441,10 +446,12 @@ bool spmm_supported(xct_dtype storage, int st) {
 }
 
 int pick_slices_per_tile(xct_dtype storage, int S) {
-  // 128-byte staged rows at most; FP32 staged rows of 16-bit matrices at
-  // least 32 bytes (the persistent kernel is their only form)
+  // staged rows of 16 to 128 bytes, the widths of the persistent kernel (a
+  // few slices run as 8 binary16 / 4 FP32 ones: the matrix stream, not the
+  // slices, sets the time there); FP32 staged rows of 16-bit matrices at
+  // least 32 bytes
   const int maxst = stages16(storage) ? 64 : 32;
-  int st = matrix16(storage) && !stages16(storage) ? 8 : 1;
+  int st = stages16(storage) ? 8 : (matrix16(storage) ? 8 : 4);
   while (st < S && st < maxst) st <<= 1;
   return st;
 }
@@ -460,8 +467,9 @@ xct_status spmm_stage(const SpmmArgs& a, cudaStream_t s) {
 }
 
 xct_status spmm_run(const SpmmArgs& a, cudaStream_t s) {
-  if (a.L->cap > 65535) {
-    set_error("stage capacity %d exceeds the 16-bit index", a.L->cap);
+  if (a.L->cap > kMaxStageCap) {
+    set_error("stage capacity %d exceeds the 16-bit staged-row offset (at most %d)", a.L->cap,
+              kMaxStageCap);
     return XCT_ERR_UNSUPPORTED;
   }
   if (!valid_storage(a.storage)) {

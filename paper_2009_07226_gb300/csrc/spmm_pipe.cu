@@ -26,6 +26,8 @@
 // runs out sets the caller's error flag, waits (bounded) for the copies this
 // CTA has in flight and returns.  The consumers' block-end rendezvous is an
 // mbarrier too, so no warp can be left at an unbounded barrier.
+#include <type_traits>
+
 #include "xct_internal.cuh"
 
 namespace xct {
@@ -42,16 +44,21 @@ struct PCfg {
   static constexpr int XB = PBytes<TX>::v;
   static constexpr int PIXB = ST * XB;
   static constexpr int VB = 16;
-  static constexpr int LPR = PIXB >= 128 ? 8 : PIXB / 16;
+  static constexpr int LPR = PIXB >= 128 ? 8 : PIXB / 16;   // lanes holding slices of a row
+  // lanes splitting a row's chunks of 4 entries (lane e takes entry e of
+  // every chunk; their partial sums are added at the block end): 16-byte
+  // staged rows keep 8 consumer warps per block this way instead of 2
+  static constexpr int ES = PIXB == 16 ? 4 : 1;
   static constexpr int VPL = PIXB / (VB * LPR);
   static constexpr int EPV = VB / XB;
   static constexpr int SPL = EPV * VPL;
-  static constexpr int RPW = 32 / LPR;
+  static constexpr int RPW = 32 / (LPR * ES);
   static constexpr int NC = kRowsPerBlock / RPW;   // consumer warps
   static constexpr int NT = (NC + 1) * 32;         // + one producer warp
   static constexpr bool X16 = XB == 2;             // normalised 16-bit staged rows
   static constexpr bool W16 = PBytes<TW>::v == 2;  // {u16 index, 16-bit value} entries
   static constexpr int EB = W16 ? 4 : 8;           // bytes per packed entry
+  static constexpr int OSH = entry_shift(PIXB);    // entry offset -> this row size
   // CTAs per SM: narrower staged rows mean fewer consumer warps per CTA
   // and smaller stage buffers, so more CTAs share an SM
   static constexpr int MINB = PIXB >= 128 ? 2 : (PIXB == 64 ? 3 : 4);
@@ -222,6 +229,13 @@ template <int EPV> struct PFma<__nv_bfloat16, __nv_bfloat16, EPV> {
           : "r"(x[e]), "h"(w));
   }
 };
+
+// staged-row byte offset (at 128 bytes per row) and value bits of one packed
+// entry: {16-bit value, u16 offset} or {u32 offset, f32 value}
+__device__ __forceinline__ uint32_t eoff(uint32_t e) { return e >> 16; }
+__device__ __forceinline__ uint32_t eval(uint32_t e) { return e & 0xffffu; }
+__device__ __forceinline__ uint32_t eoff(uint2 e) { return e.x; }
+__device__ __forceinline__ uint32_t eval(uint2 e) { return e.y; }
 
 __device__ __forceinline__ int ceil_log2_exp_p(float m) {
   if (!(m > 0.0f)) return 0;
@@ -406,7 +420,7 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
   }
 
   // ------------------------------ consumers ------------------------------
-  const int rw = lane / C::LPR, sub = lane % C::LPR;
+  const int rw = lane / (C::LPR * C::ES), el = (lane / C::LPR) % C::ES, sub = lane % C::LPR;
   const int rb = warp * C::RPW + rw;
   const int quad = rb >> 2, gq = rb & 3;
   float acc[C::SPL];
@@ -434,7 +448,28 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
       const int cnt = (int)((cw >> ((gq & 1) * 16)) & 0xffffu);
       const int nch = (cnt + 3) >> 2;
       const unsigned char* xs = xbuf(buf) + sub * C::VB;
-      if constexpr (C::W16) {
+      if constexpr (C::ES > 1) {
+        // one entry of each chunk per lane; four chunks in flight per step
+        using E = typename std::conditional<C::W16, uint32_t, uint2>::type;
+        const E* ep = reinterpret_cast<const E*>(ebuf(buf) + (off - base) * C::EB) + gq * 4 + el;
+        int c = 0;
+        for (; c + 4 <= nch; c += 4) {
+          E ev[4];
+          uint4 xv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ev[q] = ep[(c + q) * 16];
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            xv[q] = *reinterpret_cast<const uint4*>(xs + (eoff(ev[q]) >> C::OSH));
+#pragma unroll
+          for (int q = 0; q < 4; ++q) PFma<TX, TW, C::EPV>::run(acc, xv[q], eval(ev[q]));
+        }
+        for (; c < nch; ++c) {
+          const E ev = ep[c * 16];
+          const uint4 xv = *reinterpret_cast<const uint4*>(xs + (eoff(ev) >> C::OSH));
+          PFma<TX, TW, C::EPV>::run(acc, xv, eval(ev));
+        }
+      } else if constexpr (C::W16) {
         const uint4* ep = reinterpret_cast<const uint4*>(ebuf(buf) + (off - base) * 4) + gq;
         uint4 nx = nch > 0 ? ep[0] : make_uint4(0, 0, 0, 0);
         for (int c = 0; c < nch; ++c) {
@@ -446,13 +481,13 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
           for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int v = 0; v < C::VPL; ++v)
-              xv[q][v] = *reinterpret_cast<const uint4*>(xs + (size_t)(e4[q] & 0xffffu) * C::PIXB +
+              xv[q][v] = *reinterpret_cast<const uint4*>(xs + (e4[q] >> (16 + C::OSH)) +
                                                          v * C::LPR * C::VB);
 #pragma unroll
           for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int v = 0; v < C::VPL; ++v)
-              PFma<TX, TW, C::EPV>::run(acc + v * C::EPV, xv[q][v], e4[q] >> 16);
+              PFma<TX, TW, C::EPV>::run(acc + v * C::EPV, xv[q][v], e4[q] & 0xffffu);
         }
       } else {
         const uint4* ep = reinterpret_cast<const uint4*>(ebuf(buf) + (off - base) * 8) + gq * 2;
@@ -468,7 +503,7 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
           for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int v = 0; v < C::VPL; ++v)
-              xv[q][v] = *reinterpret_cast<const uint4*>(xs + (size_t)idx[q] * C::PIXB + v * C::LPR * C::VB);
+              xv[q][v] = *reinterpret_cast<const uint4*>(xs + (idx[q] >> C::OSH) + v * C::LPR * C::VB);
 #pragma unroll
           for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -485,6 +520,13 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
       const int tile = h.work / P.nblocks, b = h.work % P.nblocks;
       const int64_t row = (int64_t)b * kRowsPerBlock + rb;
       float* yt = P.y + (size_t)tile * P.nrows * ST;
+      if constexpr (C::ES > 1) {
+        // the row's partial sums of the ES lanes (fixed order: a butterfly)
+#pragma unroll
+        for (int o = C::LPR; o < C::LPR * C::ES; o <<= 1)
+#pragma unroll
+          for (int i = 0; i < C::SPL; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+      }
       float r[C::SPL];
 #pragma unroll
       for (int v = 0; v < C::VPL; ++v)
@@ -499,7 +541,7 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
             scale = ldexpf(1.0f, -P.mat_scale_exp);
           r[v * C::EPV + e] = acc[v * C::EPV + e] * scale;
         }
-      if (row < P.nrows) {
+      if (row < P.nrows && el == 0) {
 #pragma unroll
         for (int v = 0; v < C::VPL; ++v) {
           float* dst = yt + (size_t)row * ST + v * C::LPR * C::EPV + sub * C::EPV;
@@ -518,7 +560,7 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
 #pragma unroll
         for (int i = 0; i < C::SPL; ++i) d[i] = (double)r[i] * (double)r[i];
 #pragma unroll
-        for (int o = C::LPR; o < 32; o <<= 1)
+        for (int o = C::LPR * C::ES; o < 32; o <<= 1)
 #pragma unroll
           for (int i = 0; i < C::SPL; ++i) d[i] += __shfl_xor_sync(0xffffffffu, d[i], o);
         // the staged rows of this buffer are no longer read once every
@@ -533,7 +575,7 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
           if (lane == 0) atomicExch(a.err, 1);
           return;
         }
-        if (rw == 0) {
+        if (rw == 0 && el == 0) {
 #pragma unroll
           for (int v = 0; v < C::VPL; ++v)
 #pragma unroll
@@ -656,8 +698,8 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
 
 template <class TX, class TW>
 xct_status dispatch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
-  // the persistent form is built for staged rows of 32, 64 or 128 bytes
-  // (16, 32 or 64 slices in 16 bits; 8, 16 or 32 in FP32)
+  // the persistent form is built for staged rows of 16, 32, 64 or 128 bytes
+  // (8, 16, 32 or 64 slices in 16 bits; 4, 8, 16 or 32 in FP32)
   for (int i = 1; i < count; ++i)
     if (list[i].st != list[0].st) {
       set_error("persistent product: products of one launch must share the tile width");
@@ -667,6 +709,7 @@ xct_status dispatch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
     case 128: return launch_pipe<TX, TW, 128 / PBytes<TX>::v>(list, count, st);
     case 64: return launch_pipe<TX, TW, 64 / PBytes<TX>::v>(list, count, st);
     case 32: return launch_pipe<TX, TW, 32 / PBytes<TX>::v>(list, count, st);
+    case 16: return launch_pipe<TX, TW, 16 / PBytes<TX>::v>(list, count, st);
     default:
       set_error("persistent product: unsupported tile width %d", list[0].st);
       return XCT_ERR_UNSUPPORTED;
@@ -694,11 +737,11 @@ xct_status pipe_any(const SpmmArgs* list, int count, cudaStream_t s) {
 
 }  // namespace
 
-// The persistent form needs 16-byte lane vectors, staged rows of 32, 64 or
-// 128 bytes and two buffers in the shared memory of one of its CTAs.
+// The persistent form needs 16-byte lane vectors, staged rows of 16, 32, 64
+// or 128 bytes and two buffers in the shared memory of one of its CTAs.
 bool spmm_pipe_applies(const SpmmArgs& a) {
   const int pixb = a.st * (stages16(a.storage) ? 2 : 4);
-  if ((pixb != 128 && pixb != 64 && pixb != 32) || !a.work || !a.err) return false;
+  if ((pixb != 128 && pixb != 64 && pixb != 32 && pixb != 16) || !a.work || !a.err) return false;
   if (a.L->nblocks == 0) return false;
   return pipe_smem_bytes(a.L->cap, a.L->emax_slots, a.L->run_max, pixb,
                          a.storage == XCT_F32 ? 8 : 4, nullptr, nullptr, nullptr) <=

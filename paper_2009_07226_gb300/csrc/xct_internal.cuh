@@ -106,6 +106,20 @@ inline bool valid_storage(int t) { return t >= XCT_F32 && t <= XCT_BF16A; }
 constexpr int kRowsPerBlock = 64;              // rows of one thread block
 constexpr int kQuads = kRowsPerBlock / 4;      // 4-row groups per block
 
+// Packed entries name their staged row by its byte offset at 128 bytes per
+// row (position * 128): a tile with PIXB-byte staged rows finds the row at
+// offset >> log2(128 / PIXB), one shift-add per entry.  16-bit entries hold
+// {value bits (low 16), offset (high 16)}, FP32 entries {offset (low 32),
+// value bits (high 32)}.  The offset of the zero slot (position cap) must fit
+// in 16 bits.
+constexpr int kEntryRowBytes = 128;
+constexpr int kMaxStageCap = 65535 / kEntryRowBytes - 1;
+// log2(128 / pixb) for staged rows of pixb = 2 .. 128 bytes
+__host__ __device__ constexpr int entry_shift(int pixb) {
+  return pixb >= 128 ? 0 : pixb == 64 ? 1 : pixb == 32 ? 2 : pixb == 16 ? 3 : pixb == 8 ? 4
+       : pixb == 4 ? 5 : 6;
+}
+
 // One (stage, quad) segment: the entries of 4 consecutive rows interleaved in
 // chunks of 4 entries; `off` counts entries from the start of `ent`.
 struct __align__(16) Seg {
