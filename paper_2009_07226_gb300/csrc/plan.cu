@@ -685,6 +685,15 @@ __global__ void stage_pix_kernel(const int64_t* blk_stage, const int64_t* fp_off
     stage_pix[s] = fp_off[b] + (s - blk_stage[b]) * cap;
 }
 
+// staged rows of each stage (the last stage of a block holds the rest)
+__global__ void stage_np_kernel(const int64_t* blk_stage, const int64_t* fp_size, int32_t nblocks,
+                                int32_t cap, int32_t* stage_np) {
+  int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (b >= nblocks) return;
+  for (int64_t s = blk_stage[b]; s < blk_stage[b + 1]; ++s)
+    stage_np[s] = (int32_t)min((int64_t)cap, fp_size[b] - (s - blk_stage[b]) * cap);
+}
+
 // Contiguous runs of each stage's staged rows, for one bulk copy per run:
 // pairs (first row id, first position in the stage), then a closing pair
 // (-1, rows of the stage) repeated to an even count (16-byte aligned lists).
@@ -776,6 +785,30 @@ __global__ void stage_ent_kernel(const int64_t* slot_off, int64_t nstages, int64
 
 // every slot starts as a padding entry: the zero slot (position `zero_slot`)
 // with value 0
+// one descriptor per stage (see StageDescHead)
+__global__ void desc_fill_kernel(const int64_t* stage_ent, const int32_t* stage_np,
+                                 const int64_t* stage_run, const int2* runs, const Seg* seg,
+                                 int64_t nstages, int64_t run_stride, int64_t desc_bytes,
+                                 unsigned char* desc) {
+  for (int64_t st = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; st < nstages;
+       st += (int64_t)gridDim.x * blockDim.x) {
+    unsigned char* d = desc + st * desc_bytes;
+    StageDescHead h;
+    h.e0 = stage_ent[st];
+    h.slots = (uint32_t)(stage_ent[st + 1] - stage_ent[st]);
+    h.np = (uint16_t)stage_np[st];
+    const int64_t r0 = stage_run[st], nr = stage_run[st + 1] - r0;
+    h.nr = (uint16_t)nr;
+    *reinterpret_cast<StageDescHead*>(d) = h;
+    uint4* sd = reinterpret_cast<uint4*>(d + sizeof(StageDescHead));
+    const uint4* ss = reinterpret_cast<const uint4*>(seg + st * kQuads);
+    for (int q = 0; q < kQuads; ++q) sd[q] = ss[q];
+    int2* rd = reinterpret_cast<int2*>(d + sizeof(StageDescHead) + kQuads * 16);
+    for (int64_t k = 0; k < run_stride; ++k)
+      rd[k] = k < nr ? runs[r0 + k] : make_int2(-1, (int)h.np);
+  }
+}
+
 template <int EB>
 __global__ void pad_fill_kernel(void* ent, int64_t nslots, uint32_t zero_slot) {
   const uint32_t off = zero_slot * (uint32_t)kEntryRowBytes;
@@ -885,6 +918,11 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
   XCT_TRY(tmp.get(&slot_off, L.nstages * kQuads + 1));
   stage_pix_kernel<<<grid_for(nb + 1, 256), 256, 0, s>>>(L.blk_stage, fp_off, nb, cap, L.stage_pix);
   count_launch();
+  XCT_TRY(own.get(&L.stage_np, L.nstages));
+  if (nb > 0) {
+    stage_np_kernel<<<grid_for(nb, 256), 256, 0, s>>>(L.blk_stage, fp_size, nb, cap, L.stage_np);
+    count_launch();
+  }
   {
     int64_t* nrun;
     unsigned long long* rmax;
@@ -956,10 +994,23 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
       fill_entries_kernel<2><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent);
     count_launch();
   }
+  // stage descriptors: run lists padded to an even count of at least 2
+  {
+    const int64_t stride = L.run_max < 2 ? 2 : (L.run_max + 1) & ~(int64_t)1;
+    L.desc_bytes = stage_desc_bytes(stride);
+    XCT_TRY(own.get(&L.desc, (size_t)(L.nstages > 0 ? L.nstages : 1) * L.desc_bytes));
+    if (L.nstages > 0) {
+      desc_fill_kernel<<<grid_for(L.nstages, 128, 152 * 16), 128, 0, s>>>(
+          L.stage_ent, L.stage_np, L.stage_run, L.runs, L.seg, L.nstages, stride, L.desc_bytes,
+          L.desc);
+      count_launch();
+    }
+  }
   XCT_TRY_CUDA(cudaGetLastError());
   XCT_TRY_CUDA(cudaStreamSynchronize(s));
-  L.bytes = (int64_t)L.nslots * L.ebytes + L.nstages * (int64_t)sizeof(Seg) +
-            (L.nstages + 1) * 24 + (int64_t)(nb + 1) * 8 + total_fp * 4 + L.nruns * 8;
+  L.bytes = (int64_t)L.nslots * L.ebytes + L.nstages * kQuads * (int64_t)sizeof(Seg) +
+            (L.nstages + 1) * 24 + L.nstages * 4 + (int64_t)(nb + 1) * 8 + total_fp * 4 +
+            L.nruns * 8 + L.nstages * L.desc_bytes;
   own.move_to(keep);
   return XCT_OK;
 }

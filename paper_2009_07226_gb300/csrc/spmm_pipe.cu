@@ -59,10 +59,16 @@ struct PCfg {
   static constexpr bool W16 = PBytes<TW>::v == 2;  // {u16 index, 16-bit value} entries
   static constexpr int EB = W16 ? 4 : 8;           // bytes per packed entry
   static constexpr int OSH = entry_shift(PIXB);    // entry offset -> this row size
+  static constexpr int NB = PIXB == 16 ? kPipeBufs16 : kPipeBufs;   // stage buffers
   // CTAs per SM: narrower staged rows mean fewer consumer warps per CTA
   // and smaller stage buffers, so more CTAs share an SM
-  static constexpr int MINB = PIXB >= 128 ? 2 : (PIXB == 64 ? 3 : 4);
+  static constexpr int MINB = PIXB >= 128 ? 2 : (PIXB == 64 ? 3 : (PIXB == 16 ? kPipeMinb16 : 4));
 };
+
+// stage descriptors are requested this many stages before the stage's
+// copies, into kDescSlots = kDescAhead + 1 slots
+constexpr int kDescAhead = 3;
+constexpr int kDescSlots = kDescAhead + 1;
 
 struct __align__(16) Hdr {
   int32_t work;    // work item inside its product (tile * nblocks + block), -1 = no more work
@@ -76,10 +82,8 @@ struct __align__(16) Hdr {
 // One product of a launch: a layout with its input / output vectors.
 struct PipeLayout {
   const int64_t* blk_stage;
-  const int64_t* stage_run;
-  const int64_t* stage_ent;
-  const int2* runs;
-  const Seg* seg;
+  const unsigned char* desc;  // [nstages] stage descriptors (StageDescHead ...)
+  int64_t desc_bytes;
   const unsigned char* ent;
   int64_t nrows, ncols;
   int cap, nblocks, ntiles;
@@ -96,7 +100,7 @@ struct PipeArgs {
   int nl;                    // products in this launch
   int nwork;                 // work items over all products
   int cap;                   // largest stage capacity (buffer rows)
-  uint32_t listbytes;        // per-slot run-list region (128-byte multiple)
+  uint32_t dbytes;           // per-slot descriptor region (128-byte multiple)
   int* work;
   int* err;
   uint32_t xbytes, ebytes;   // per-buffer region sizes (128-byte multiples)
@@ -250,14 +254,16 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
   using C = PCfg<TX, TW, ST>;
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t bufbytes = a.xbytes + a.ebytes + 256 + 128;
-  const uint32_t listbytes = a.listbytes;
-  constexpr int NB = kPipeBufs;
-  int2* lists = reinterpret_cast<int2*>(smem + NB * bufbytes);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + NB * bufbytes + NB * listbytes);
+  constexpr int NB = C::NB;
+  constexpr int DS = kDescSlots;
+  // [NB stage buffers][DS descriptor slots][barriers][DS stage identities]
+  unsigned char* dslots = smem + NB * bufbytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(dslots + DS * a.dbytes);
   uint64_t* empty = full + NB;
-  uint64_t* plbar = full + 2 * NB;   // run list of a stage landed
-  uint64_t* redbar = full + 3 * NB;  // consumers' rendezvous at a block end (2)
-  auto plist = [&](int slot) { return lists + (size_t)slot * (listbytes / 8); };
+  uint64_t* dbar = full + 2 * NB;        // descriptor of a stage landed
+  uint64_t* redbar = full + 2 * NB + DS;  // consumers' rendezvous at a block end (2)
+  int4* ident = reinterpret_cast<int4*>(redbar + 2);
+  auto dslot = [&](int k) { return dslots + (size_t)k * a.dbytes; };
   auto xbuf = [&](int b) { return smem + b * bufbytes; };
   auto ebuf = [&](int b) { return smem + b * bufbytes + a.xbytes; };
   auto sbuf = [&](int b) { return smem + b * bufbytes + a.xbytes + a.ebytes; };
@@ -268,8 +274,8 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
     for (int b = 0; b < NB; ++b) {
       mbar_init(&full[b], 1);
       mbar_init(&empty[b], C::NC);
-      mbar_init(&plbar[b], 1);
     }
+    for (int k = 0; k < kDescSlots; ++k) mbar_init(&dbar[k], 1);
     mbar_init(&redbar[0], C::NC);
     mbar_init(&redbar[1], C::NC);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -285,111 +291,139 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
 
   if (warp == C::NC) {
     // ----------------------------- producer -----------------------------
-    // A stage reference: work item of the launch (-1: no more), its product
-    // and its work item inside the product, stage index in its block, stages
-    // in the block, layout stage (-1 for a block without entries), and the
-    // stage's staged rows and packed entries (loaded when the reference is
-    // made, one stage ahead of its copies).
-    struct Ref {
-      int w, l, wl, k, nst;
-      int64_t s;
-      int64_t r0, e0;
-      int nr, np;
-      uint32_t eb;
-      uint2 seg;   // this lane's 8 bytes of the stage's 16 segment headers
+    // A cursor walks the stages of the CTA's blocks: work item of the launch
+    // (-1: no more), its product and work item inside the product, stage
+    // index in its block, stages in the block, layout stage (-1 for a block
+    // without entries).  Each stage's descriptor (one bulk copy from an
+    // array of fixed stride, so its address needs only the stage index) is
+    // requested kDescAhead stages before the stage's copies are issued, and
+    // the next block is claimed from the work counter one block ahead (lane
+    // 0 holds the counter's answer until it is needed): no metadata load is
+    // on the path of a stage.
+    struct Cursor {
+      int w, l, wl, k, nst, s;
     };
-    auto meta = [&](Ref& r) {
-      r.r0 = 0; r.e0 = 0; r.nr = 0; r.np = 0; r.eb = 0;
-      if (r.w >= 0 && r.s >= 0) {
-        const PipeLayout& P = a.L[r.l];
-        r.seg = reinterpret_cast<const uint2*>(P.seg + r.s * kQuads)[lane];
-        r.r0 = P.stage_run[r.s];
-        r.nr = (int)(P.stage_run[r.s + 1] - r.r0);
-        r.np = P.runs[r.r0 + r.nr - 1].y;   // the closing pair holds the row count
-        r.e0 = P.stage_ent[r.s];
-        r.eb = (uint32_t)((P.stage_ent[r.s + 1] - r.e0) * C::EB);
+    struct Claim {
+      int raw;      // lane 0: the work counter's answer
+      int age;      // stages since the claim
+      bool resolved;
+      int w, l, wl;
+      int64_t s0, s1;
+    };
+    auto claim = [&]() -> Claim {
+      Claim c{0, 0, false, -1, 0, 0, 0, 0};
+      if (lane == 0) c.raw = atomicAdd(a.work, 1);
+      return c;
+    };
+    auto resolve = [&](Claim& c) {
+      if (c.resolved) return;
+      c.resolved = true;
+      c.w = __shfl_sync(0xffffffffu, c.raw, 0);
+      if (c.w >= nwork) {
+        c.w = -1;
+        return;
       }
-    };
-    auto fetch = [&]() -> Ref {
-      int w = 0;
-      if (lane == 0) w = atomicAdd(a.work, 1);
-      w = __shfl_sync(0xffffffffu, w, 0);
-      Ref r{-1, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0u};
-      if (w >= nwork) return r;
       int l = a.nl - 1;
-      while (l > 0 && w < a.L[l].work_begin) --l;
+      while (l > 0 && c.w < a.L[l].work_begin) --l;
       const PipeLayout& P = a.L[l];
-      const int wl = w - P.work_begin;
-      const int b = wl % P.nblocks;
-      const int64_t s0 = P.blk_stage[b], s1 = P.blk_stage[b + 1];
-      r = Ref{w, l, wl, 0, s1 > s0 ? (int)(s1 - s0) : 1, s1 > s0 ? s0 : (int64_t)-1, 0, 0, 0, 0, 0u};
-      meta(r);
-      return r;
+      c.l = l;
+      c.wl = c.w - P.work_begin;
+      const int b = c.wl % P.nblocks;
+      c.s0 = P.blk_stage[b];
+      c.s1 = P.blk_stage[b + 1];
     };
-    // the run list of stage r into list slot `slot` (one bulk copy; lists
-    // hold an even number of 8-byte pairs, so 16-byte multiples)
-    auto request = [&](const Ref& r, int slot) {
+    auto start_of = [&](const Claim& c) -> Cursor {
+      if (c.w < 0) return Cursor{-1, 0, 0, 0, 1, -1};
+      return Cursor{c.w, c.l, c.wl, 0, c.s1 > c.s0 ? (int)(c.s1 - c.s0) : 1,
+                    c.s1 > c.s0 ? (int)c.s0 : -1};
+    };
+    Claim pend = claim();
+    resolve(pend);
+    Cursor cur = start_of(pend);
+    if (pend.w >= 0) pend = claim();
+    auto advance = [&](Cursor& c) {
+      if (c.w < 0) return;
+      if (c.k + 1 < c.nst) {
+        ++c.k;
+        if (c.s >= 0) ++c.s;
+        return;
+      }
+      resolve(pend);
+      c = start_of(pend);
+      if (pend.w >= 0) pend = claim();
+    };
+    // the descriptor of the cursor's stage into slot k, with the stage's
+    // identity (work item in its product or -1, product, stage in block,
+    // flags: 1 = last stage of its block, 2 = has entries)
+    auto request = [&](const Cursor& c, int k) {
       if (lane != 0) return;
-      if (r.w >= 0 && r.s >= 0) {
-        mbar_arrive_tx(&plbar[slot], (uint32_t)r.nr * 8u);
-        bulk_g2s(plist(slot), a.L[r.l].runs + r.r0, (uint32_t)r.nr * 8u, &plbar[slot]);
+      const bool real = c.w >= 0 && c.s >= 0;
+      ident[k] = make_int4(c.w >= 0 ? c.wl : -1, c.l, c.k,
+                           (c.k == c.nst - 1 ? 1 : 0) | (real ? 2 : 0));
+      if (real) {
+        const PipeLayout& P = a.L[c.l];
+        mbar_arrive_tx(&dbar[k], (uint32_t)P.desc_bytes);
+        bulk_g2s(dslot(k), P.desc + (size_t)c.s * P.desc_bytes, (uint32_t)P.desc_bytes, &dbar[k]);
       } else {
-        mbar_arrive(&plbar[slot]);
+        mbar_arrive(&dbar[k]);
       }
     };
     bool ok = true;
-    uint32_t fail_it = 0, req_hi = 0;   // req_hi: last stage whose run list was requested
-    Ref cur = fetch();
-    request(cur, 0);
+    uint32_t fail_it = 0, req_hi = 0;   // req_hi: last stage whose descriptor was requested
+    for (int j = 0; j < kDescAhead; ++j) {
+      request(cur, j);
+      advance(cur);
+    }
+    req_hi = kDescAhead - 1;
     for (uint32_t it = 0;; ++it) {
       const int buf = (int)(it % NB);
       const uint32_t use = it / NB;
-      Ref nxt{-1, 0, 0, 0, 1, -1, 0, 0, 0, 0, 0u};
-      if (cur.w >= 0) {
-        if (cur.k + 1 < cur.nst) {
-          nxt = Ref{cur.w, cur.l, cur.wl, cur.k + 1, cur.nst, cur.s >= 0 ? cur.s + 1 : -1, 0, 0, 0, 0, 0u};
-          meta(nxt);
-        } else {
-          nxt = fetch();
-        }
-        // this warp's reads of the next list slot (stage it+1-NB) precede
-        // the copy into it
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        request(nxt, buf + 1 == NB ? 0 : buf + 1);
-        req_hi = it + 1;
-      }
+      const int ds = (int)(it % DS);
+      // the claim made at the last block crossing: its answer has had two
+      // stages to arrive
+      if (!pend.resolved && ++pend.age >= 2) resolve(pend);
+      // slot (it + kDescAhead) % DS last held stage it - 1, read by now;
+      // this warp's reads of it precede the copy into it
+      __syncwarp();
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      request(cur, (int)((it + kDescAhead) % DS));
+      req_hi = it + kDescAhead;
+      advance(cur);
       if (!mbar_wait(&empty[buf], (use & 1) ^ 1, a.wait_ns)) { ok = false; fail_it = it; break; }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      const bool real = cur.w >= 0 && cur.s >= 0;
-      if (real && !mbar_wait(&plbar[buf], use & 1, a.wait_ns)) { ok = false; fail_it = it; break; }
-      const PipeLayout& P = a.L[cur.l];
-      const int tile = cur.w >= 0 ? cur.wl / P.nblocks : 0;
-      const unsigned char* xt = P.xs + (size_t)tile * P.ncols * C::PIXB;
-      const int np = real ? cur.np : 0;
-      const uint32_t eb = real ? cur.eb : 0u;
+      if (!mbar_wait(&dbar[ds], (it / DS) & 1, a.wait_ns)) { ok = false; fail_it = it; break; }
+      __syncwarp();
+      const int4 id = ident[ds];
+      const bool real = (id.w & 2) != 0;
+      const PipeLayout& P = a.L[id.y];
+      const unsigned char* dd = dslot(ds);
+      const StageDescHead dh = *reinterpret_cast<const StageDescHead*>(dd);
+      const int np = real ? (int)dh.np : 0;
+      const uint32_t eb = real ? dh.slots * (uint32_t)C::EB : 0u;
       if (lane == 0) {
         Hdr h;
-        h.work = cur.w >= 0 ? cur.wl : -1;
-        h.prod = cur.l;
-        h.kstage = cur.k;
-        h.last = (cur.k == cur.nst - 1);
+        h.work = id.x;
+        h.prod = id.y;
+        h.kstage = id.z;
+        h.last = id.w & 1;
         h.np = np;
         *hbuf(buf) = h;
       }
       if (real) {
+        const int tile = id.x / P.nblocks;
+        const unsigned char* xt = P.xs + (size_t)tile * P.ncols * C::PIXB;
         // one bulk copy per contiguous run of staged rows, plus the stage's
         // packed entries, all counted in bytes on the full barrier (the
         // expected count is set before any copy starts)
         if (lane == 0) mbar_expect_tx(&full[buf], (uint32_t)np * C::PIXB + eb);
-        // the segment headers, loaded into the lanes' registers when the
-        // stage reference was made, go in by plain stores (the full
-        // barrier's arrival below publishes them with the header): one TMA
-        // request less per stage
-        reinterpret_cast<uint2*>(sbuf(buf))[lane] = cur.seg;
+        // the segment headers, from the descriptor, by plain stores (the
+        // full barrier's arrival below publishes them with the header)
+        reinterpret_cast<uint2*>(sbuf(buf))[lane] =
+            reinterpret_cast<const uint2*>(dd + sizeof(StageDescHead))[lane];
         __syncwarp();
-        const int2* rl = plist(buf);
+        const int2* rl = reinterpret_cast<const int2*>(dd + sizeof(StageDescHead) + kQuads * 16);
         unsigned char* xd = xbuf(buf);
-        for (int k = lane; k < cur.nr; k += 32) {
+        for (int k = lane; k < (int)dh.nr; k += 32) {
           const int2 run = rl[k];
           if (run.x >= 0) {
             const uint32_t len = (uint32_t)(rl[k + 1].y - run.y);
@@ -397,24 +431,23 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
                      &full[buf]);
           }
         }
-        if (lane == 0 && eb) bulk_g2s(ebuf(buf), P.ent + (size_t)cur.e0 * C::EB, eb, &full[buf]);
+        if (lane == 0 && eb) bulk_g2s(ebuf(buf), P.ent + (size_t)dh.e0 * C::EB, eb, &full[buf]);
       }
       // the single arrival of this phase; it also publishes the header
       __syncwarp();
       if (lane == 0) mbar_arrive(&full[buf]);
-      if (cur.w < 0) break;
-      cur = nxt;
+      if (id.x < 0) break;
     }
     if (!ok) {
       if (lane == 0) atomicExch(a.err, 1);
       // let copies already issued land before the CTA's shared memory goes
       // away: the stage copies of the last NB iterations before the failing
       // one (every iteration arrives on its full barrier, with copies or
-      // without), and the run lists requested for stages fail_it and
-      // fail_it + 1 (every request completes a phase of its list barrier)
+      // without), and the descriptors requested for stages fail_it to req_hi
+      // (every request completes a phase of its slot's barrier)
       for (uint32_t j = fail_it > (uint32_t)NB ? fail_it - NB : 0; j < fail_it; ++j)
         mbar_wait(&full[j % NB], (j / NB) & 1, kDrainNs);
-      for (uint32_t j = fail_it; j <= req_hi; ++j) mbar_wait(&plbar[j % NB], (j / NB) & 1, kDrainNs);
+      for (uint32_t j = fail_it; j <= req_hi; ++j) mbar_wait(&dbar[j % DS], (j / DS) & 1, kDrainNs);
     }
     return;
   }
@@ -428,8 +461,8 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
   for (int i = 0; i < C::SPL; ++i) acc[i] = 0.0f;
   uint32_t rphase = 0;   // phase of the block-end rendezvous barriers
   for (uint32_t it = 0;; ++it) {
-    const int buf = (int)(it % kPipeBufs);
-    if (!mbar_wait(&full[buf], (it / kPipeBufs) & 1, a.wait_ns)) {
+    const int buf = (int)(it % NB);
+    if (!mbar_wait(&full[buf], (it / NB) & 1, a.wait_ns)) {
       if (lane == 0) atomicExch(a.err, 1);
       return;
     }
@@ -606,21 +639,33 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
   }
 }
 
-size_t pipe_smem_bytes(int cap, int64_t emax, int64_t rmax, int pixb, int eb, uint32_t* xbytes,
-                       uint32_t* ebytes, uint32_t* lbytes) {
+size_t pipe_smem_bytes(int cap, int64_t emax, int64_t desc_bytes, int pixb, int eb, int nb,
+                       uint32_t* xbytes, uint32_t* ebytes, uint32_t* dbytes) {
   const size_t x = ((size_t)(cap + 1) * pixb + 127) / 128 * 128;
   const size_t e = ((size_t)emax * eb + 127) / 128 * 128;
-  const size_t list = ((size_t)rmax * 8 + 127) / 128 * 128;
+  const size_t d = ((size_t)desc_bytes + 127) / 128 * 128;
   if (xbytes) *xbytes = (uint32_t)x;
   if (ebytes) *ebytes = (uint32_t)e;
-  if (lbytes) *lbytes = (uint32_t)list;
-  return kPipeBufs * (x + e + 256 + 128) + kPipeBufs * list + 128;
+  if (dbytes) *dbytes = (uint32_t)d;
+  // stage buffers, descriptor slots, barriers, stage identities
+  return nb * (x + e + 256 + 128) + kDescSlots * d + 8 * (2 * nb + kDescSlots + 2) +
+         16 * kDescSlots + 128;
 }
 
 // shared memory a pipeline CTA may use so that `minb` CTAs fit on an SM
 // (228 KB per SM, 1 KB of it reserved per CTA)
 constexpr size_t pipe_cta_smem_max(int minb) { return (size_t)(228 * 1024) / minb - 1024; }
-constexpr int pipe_minb(int pixb) { return pixb >= 128 ? 2 : (pixb == 64 ? 3 : 4); }
+// The persistent form runs with at least two CTAs per SM; narrow rows whose
+// stage buffers do not fit their usual count run with as many as fit.
+constexpr int kPipeMinCtas = 2;
+inline int pipe_ctas_per_sm(size_t smem, int minb) {
+  int c = (int)((size_t)(228 * 1024) / (smem + 1024));
+  return c < minb ? c : minb;
+}
+constexpr int pipe_minb(int pixb) {
+  return pixb >= 128 ? 2 : (pixb == 64 ? 3 : (pixb == 16 ? kPipeMinb16 : 4));
+}
+constexpr int pipe_nb(int pixb) { return pixb == 16 ? kPipeBufs16 : kPipeBufs; }
 
 template <class TX, class TW, int ST>
 xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
@@ -634,16 +679,14 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   }
   PipeArgs a{};
   int work = 0, cap = 0;
-  int64_t emax = 0, rmax = 0;
+  int64_t emax = 0, dmax = 0;
   for (int i = 0; i < count; ++i) {
     const SpmmArgs& s = list[i];
     const Layout& L = *s.L;
     PipeLayout& P = a.L[i];
     P.blk_stage = L.blk_stage;
-    P.stage_run = L.stage_run;
-    P.stage_ent = L.stage_ent;
-    P.runs = L.runs;
-    P.seg = L.seg;
+    P.desc = L.desc;
+    P.desc_bytes = L.desc_bytes;
     P.ent = static_cast<const unsigned char*>(L.ent);
     P.nrows = L.nrows;
     P.ncols = L.ncols;
@@ -660,7 +703,7 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
     work += L.nblocks * s.ntiles;
     cap = cap > L.cap ? cap : L.cap;
     emax = emax > L.emax_slots ? emax : L.emax_slots;
-    rmax = rmax > L.run_max ? rmax : L.run_max;
+    dmax = dmax > L.desc_bytes ? dmax : L.desc_bytes;
   }
   a.nl = count;
   a.nwork = work;
@@ -668,10 +711,12 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   a.work = list[0].work;
   a.err = list[0].err;
   a.wait_ns = wait_limit_ns();
-  const size_t smem = pipe_smem_bytes(cap, emax, rmax, C::PIXB, C::EB, &a.xbytes, &a.ebytes,
-                                      &a.listbytes);
+  static_assert(C::NB == pipe_nb(C::PIXB), "stage buffers");
+  const size_t smem = pipe_smem_bytes(cap, emax, dmax, C::PIXB, C::EB, C::NB, &a.xbytes, &a.ebytes,
+                                      &a.dbytes);
   static_assert(C::MINB == pipe_minb(C::PIXB), "CTAs per SM");
-  if (smem > pipe_cta_smem_max(C::MINB)) {
+  const int per_sm = pipe_ctas_per_sm(smem, C::MINB);
+  if (per_sm < kPipeMinCtas) {
     set_error("persistent product: %zu bytes of shared memory needed", smem);
     return XCT_ERR_UNSUPPORTED;
   }
@@ -688,7 +733,7 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   int sms = 0;
   XCT_TRY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cur_dev));
   if (work == 0) return XCT_OK;
-  const int grid = work < sms * C::MINB ? work : sms * C::MINB;
+  const int grid = work < sms * per_sm ? work : sms * per_sm;
   XCT_TRY_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int), st));
   spmm_pipe_kernel<TX, TW, ST><<<grid, C::NT, smem, st>>>(a);
   count_launch();
@@ -743,9 +788,9 @@ bool spmm_pipe_applies(const SpmmArgs& a) {
   const int pixb = a.st * (stages16(a.storage) ? 2 : 4);
   if ((pixb != 128 && pixb != 64 && pixb != 32 && pixb != 16) || !a.work || !a.err) return false;
   if (a.L->nblocks == 0) return false;
-  return pipe_smem_bytes(a.L->cap, a.L->emax_slots, a.L->run_max, pixb,
-                         a.storage == XCT_F32 ? 8 : 4, nullptr, nullptr, nullptr) <=
-         pipe_cta_smem_max(pipe_minb(pixb));
+  return pipe_smem_bytes(a.L->cap, a.L->emax_slots, a.L->desc_bytes, pixb,
+                         a.storage == XCT_F32 ? 8 : 4, pipe_nb(pixb), nullptr, nullptr, nullptr) <=
+         pipe_cta_smem_max(kPipeMinCtas);
 }
 
 xct_status spmm_pipe(const SpmmArgs& a, cudaStream_t s) { return pipe_any(&a, 1, s); }
@@ -753,18 +798,18 @@ xct_status spmm_pipe(const SpmmArgs& a, cudaStream_t s) { return pipe_any(&a, 1,
 bool spmm_pipe_multi_applies(const SpmmArgs* list, int count) {
   if (count < 1 || count > kMaxPipeProducts) return false;
   int cap = 0;
-  int64_t emax = 0, rmax = 0;
+  int64_t emax = 0, dmax = 0;
   for (int i = 0; i < count; ++i) {
     if (!spmm_pipe_applies(list[i]) || list[i].storage != list[0].storage ||
         list[i].st != list[0].st)
       return false;
     cap = cap > list[i].L->cap ? cap : list[i].L->cap;
     emax = emax > list[i].L->emax_slots ? emax : list[i].L->emax_slots;
-    rmax = rmax > list[i].L->run_max ? rmax : list[i].L->run_max;
+    dmax = dmax > list[i].L->desc_bytes ? dmax : list[i].L->desc_bytes;
   }
   const int pixb = list[0].st * (stages16(list[0].storage) ? 2 : 4);
-  return pipe_smem_bytes(cap, emax, rmax, pixb, list[0].storage == XCT_F32 ? 8 : 4, nullptr,
-                         nullptr, nullptr) <= pipe_cta_smem_max(pipe_minb(pixb));
+  return pipe_smem_bytes(cap, emax, dmax, pixb, list[0].storage == XCT_F32 ? 8 : 4, pipe_nb(pixb),
+                         nullptr, nullptr, nullptr) <= pipe_cta_smem_max(kPipeMinCtas);
 }
 
 xct_status spmm_pipe_multi(const SpmmArgs* list, int count, cudaStream_t s) {

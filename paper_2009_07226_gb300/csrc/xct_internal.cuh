@@ -127,6 +127,21 @@ struct __align__(16) Seg {
   uint16_t cnt[4];
 };
 
+// A stage descriptor: what the persistent product's producer needs about
+// one stage, stored at a fixed stride so that its address follows from the
+// stage index alone and one bulk copy, requested several stages ahead, brings
+// it in: the head, the stage's kQuads segment headers, then its run list
+// padded to the layout's longest one with closing pairs.
+struct __align__(16) StageDescHead {
+  int64_t e0;          // first packed slot of the stage
+  uint32_t slots;      // packed slots of the stage
+  uint16_t np;         // staged rows
+  uint16_t nr;         // run-list pairs (even)
+};
+inline int64_t stage_desc_bytes(int64_t run_stride) {
+  return (int64_t)sizeof(StageDescHead) + kQuads * 16 + 8 * run_stride;
+}
+
 struct Layout {
   int64_t nrows = 0, ncols = 0;
   int32_t nblocks = 0;
@@ -137,6 +152,7 @@ struct Layout {
   int64_t footprint = 0;       // staged vectors over all stages
   int64_t* blk_stage = nullptr;   // [nblocks + 1] stage ranges of the blocks
   int64_t* stage_pix = nullptr;   // [nstages + 1] offsets into pix
+  int32_t* stage_np = nullptr;    // [nstages] staged rows of each stage
   int32_t* pix = nullptr;         // staged input row ids, stage by stage
   Seg* seg = nullptr;             // [nstages * kQuads]
   void* ent = nullptr;            // packed entries
@@ -147,16 +163,20 @@ struct Layout {
   int2* runs = nullptr;           // (first row id, first position) pairs
   int64_t nruns = 0;              // pairs over all stages
   int64_t run_max = 0;            // largest stage list, in pairs
+  unsigned char* desc = nullptr;  // [nstages] stage descriptors of desc_bytes each
+  int64_t desc_bytes = 0;
   int64_t bytes = 0;
 };
 
 // Shared memory of one pipeline buffer (staged rows of `pixb` bytes, the
-// stage's packed entries, its segment headers) -- see spmm_pipe.cu.
+// stage's packed entries, its segment headers and header) with its share of
+// the stage-descriptor slots (four slots over two buffers) -- see
+// spmm_pipe.cu.
 inline size_t pipe_buffer_bytes(const Layout& L, int pixb) {
   size_t x = ((size_t)(L.cap + 1) * pixb + 127) / 128 * 128;
   size_t e = ((size_t)L.emax_slots * L.ebytes + 127) / 128 * 128;
-  size_t list = ((size_t)L.run_max * 8 + 127) / 128 * 128;
-  return x + e + list + 128 * 2 + 256;
+  size_t d = ((size_t)L.desc_bytes + 127) / 128 * 128;
+  return x + e + 2 * d + 128 * 2 + 256;
 }
 #ifndef XCT_PIPE_BUFS
 #define XCT_PIPE_BUFS 2
@@ -165,6 +185,15 @@ inline size_t pipe_buffer_bytes(const Layout& L, int pixb) {
 // stages ahead of the consumers)
 constexpr int kPipeBufs = XCT_PIPE_BUFS;
 static_assert(kPipeBufs == 2 || kPipeBufs == 3, "pipeline buffers");
+// stage buffers and CTAs per SM of the pipeline with 16-byte staged rows
+#ifndef XCT_PIPE_BUFS16
+#define XCT_PIPE_BUFS16 2
+#endif
+#ifndef XCT_PIPE_MINB16
+#define XCT_PIPE_MINB16 4
+#endif
+constexpr int kPipeBufs16 = XCT_PIPE_BUFS16;
+constexpr int kPipeMinb16 = XCT_PIPE_MINB16;
 // shared memory one pipeline CTA with 128-byte staged rows may use for its
 // buffers (two such CTAs share an SM; the rest of a CTA's 113 KB goes to the
 // barriers and run lists)
