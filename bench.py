@@ -640,12 +640,13 @@ def run_ours(args):
     #  HBM: 2 flop per matrix entry and slice over the algorithmic bytes
     fma_peak_derived = 128 * 2 * nsm * clk / 1e12
     op16_peak_derived = 64 * 2 * nsm * clk / 1e12
-    # the 16-bit operand roof measured on this GPU (the library's roof probe:
-    # the product's inner step alone); the FP32 FMA roof stays the nominal
-    # one (the probe's FP32 kind carries its index arithmetic, no clean peak)
+    # the roofs derived from the unit counts and the clock: every FMA reads
+    # 2 bytes of a staged row from shared memory (128 B/clk/SM), and FP32
+    # FMAs (128/clk/SM); the library's roof probe times the product's inner
+    # step alone on this GPU as a check of the first
     roof = _measure_roof(stream)
     fma_peak = fma_peak_derived
-    op16_peak = roof["gather16_mixed_fma"]["tflops"]
+    op16_peak = op16_peak_derived
     rows_a, cols_a = m * nd, n * n
     alg_bytes = nnz * 4 + (rows_a + 1) * 8 + S * cols_a * 2 + S * rows_a * 4
     alg_bytes_bp = nnz * 4 + (cols_a + 1) * 8 + S * rows_a * 2 + S * cols_a * 4
@@ -696,13 +697,15 @@ def run_ours(args):
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "kernel": "spmm_pipe_kernel<__half,64> (projection, 2*nnz*S flops per launch)",
-            "peak_source": (f"the least of three roofs: the product's inner step (16-byte shared-memory "
-                            f"gather of one 128-byte staged row by 8 lanes feeding 8 mixed-precision "
-                            f"FMAs) {op16_peak:.1f}, measured by the library's roof probe on this GPU "
-                            f"(derived at {sm_mhz:.0f} MHz for 64 FMA/clk/SM: {op16_peak_derived:.1f}); "
-                            f"the nominal FP32 FMA roof {fma_peak:.1f} ({nsm} SMs x 128 FMA/clk x 2 flop); "
-                            f"the HBM roof {hbm_roof:.1f} (2*nnz*S flop over the algorithmic bytes at the "
-                            f"measured {peak_hbm:.0f} GB/s)"),
+            "peak_source": (f"derived at the median SM clock {sm_mhz:.0f} MHz, the least of three roofs: "
+                            f"the 16-bit operand roof {op16_peak:.1f} (each FMA reads 2 B of a staged row "
+                            f"from shared memory at 128 B/clk/SM: {nsm} SMs x 64 FMA/clk x 2 flop), which "
+                            f"the library's roof probe reaches to "
+                            f"{roof['gather16_mixed_fma']['tflops'] / op16_peak:.0%} with the product's "
+                            f"inner step alone ({roof['gather16_mixed_fma']['tflops']:.1f} measured); the "
+                            f"FP32 FMA roof {fma_peak:.1f} ({nsm} x 128 FMA/clk x 2 flop); the HBM roof "
+                            f"{hbm_roof:.1f} (2*nnz*S flop over the algorithmic bytes at the measured "
+                            f"{peak_hbm:.0f} GB/s)"),
             "roof_probe": {k: {**v, "fma_per_clk_per_sm": (v["ops_per_s"] / (nsm * clk)
                                                            if "tflops" in v else None)}
                            for k, v in roof.items()},

@@ -44,18 +44,27 @@ struct PCfg {
   static constexpr int XB = PBytes<TX>::v;
   static constexpr int PIXB = ST * XB;
   static constexpr int VB = 16;
-  static constexpr int LPR = PIXB >= 128 ? 8 : PIXB / 16;   // lanes holding slices of a row
-  // lanes splitting a row's chunks of 4 entries (lane e takes entry e of
-  // every chunk; their partial sums are added at the block end): 16-byte
-  // staged rows keep 8 consumer warps per block this way instead of 2
-  static constexpr int ES = PIXB == 16 ? 4 : 1;
+  static constexpr bool X16 = XB == 2;             // normalised 16-bit staged rows
+  static constexpr int LPR = PIXB >= 128 ? (X16 ? 4 : 8) : PIXB / 16;   // lanes holding slices of a row
+  // lanes splitting a row's chunks of 4 entries (lane e takes 4 / ES
+  // consecutive entries of every chunk; their partial sums are added at the
+  // block end): 16-byte staged rows keep 8 consumer warps per block this way
+  // instead of 2; 128-byte rows of 16-bit slices give each lane 16 slices
+  // of a row (two 16-byte vectors per entry), so the per-entry work
+  // (offset, address, entry load) is shared by twice the FMAs (1.4% faster
+  // binary16 products; FP32 rows measured slower this way and keep 8 lanes
+  // of 4 slices)
+  static constexpr int ES = PIXB == 16 ? 4 : (PIXB >= 128 && X16 ? 2 : 1);
   static constexpr int VPL = PIXB / (VB * LPR);
+  // with two lanes per row and two vectors per lane, lane e reads half e of
+  // the staged row first, so the two rows a quarter warp reads at once fall
+  // in different banks; its accumulators acc[0 .. EPV) hold half e
+  static constexpr bool SWZ = ES == 2 && VPL == 2;
   static constexpr int EPV = VB / XB;
   static constexpr int SPL = EPV * VPL;
   static constexpr int RPW = 32 / (LPR * ES);
   static constexpr int NC = kRowsPerBlock / RPW;   // consumer warps
   static constexpr int NT = (NC + 1) * 32;         // + one producer warp
-  static constexpr bool X16 = XB == 2;             // normalised 16-bit staged rows
   static constexpr bool W16 = PBytes<TW>::v == 2;  // {u16 index, 16-bit value} entries
   static constexpr int EB = W16 ? 4 : 8;           // bytes per packed entry
   static constexpr int OSH = entry_shift(PIXB);    // entry offset -> this row size
@@ -482,25 +491,42 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
       const int nch = (cnt + 3) >> 2;
       const unsigned char* xs = xbuf(buf) + sub * C::VB;
       if constexpr (C::ES > 1) {
-        // one entry of each chunk per lane; four chunks in flight per step
+        // EPL entries of each chunk per lane; four entries in flight per step
+        constexpr int EPL = 4 / C::ES;
+        constexpr int U = 4 / EPL;   // chunks per step
         using E = typename std::conditional<C::W16, uint32_t, uint2>::type;
-        const E* ep = reinterpret_cast<const E*>(ebuf(buf) + (off - base) * C::EB) + gq * 4 + el;
+        const E* ep = reinterpret_cast<const E*>(ebuf(buf) + (off - base) * C::EB) + gq * 4 + el * EPL;
+        const unsigned char* x0 = xs + (C::SWZ ? el : 0) * C::LPR * C::VB;
+        const unsigned char* x1 = xs + (C::SWZ ? 1 - el : 1) * C::LPR * C::VB;
         int c = 0;
-        for (; c + 4 <= nch; c += 4) {
+        for (; c + U <= nch; c += U) {
           E ev[4];
-          uint4 xv[4];
+          uint4 xa[4], xb[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) ev[q] = ep[(c + q) * 16];
+          for (int u = 0; u < U; ++u)
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            xv[q] = *reinterpret_cast<const uint4*>(xs + (eoff(ev[q]) >> C::OSH));
+            for (int j = 0; j < EPL; ++j) ev[u * EPL + j] = ep[(c + u) * 16 + j];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) PFma<TX, TW, C::EPV>::run(acc, xv[q], eval(ev[q]));
+          for (int q = 0; q < 4; ++q) {
+            const uint32_t o = eoff(ev[q]) >> C::OSH;
+            xa[q] = *reinterpret_cast<const uint4*>(x0 + o);
+            if constexpr (C::VPL == 2) xb[q] = *reinterpret_cast<const uint4*>(x1 + o);
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            PFma<TX, TW, C::EPV>::run(acc, xa[q], eval(ev[q]));
+            if constexpr (C::VPL == 2) PFma<TX, TW, C::EPV>::run(acc + C::EPV, xb[q], eval(ev[q]));
+          }
         }
         for (; c < nch; ++c) {
-          const E ev = ep[c * 16];
-          const uint4 xv = *reinterpret_cast<const uint4*>(xs + (eoff(ev) >> C::OSH));
-          PFma<TX, TW, C::EPV>::run(acc, xv, eval(ev));
+#pragma unroll
+          for (int j = 0; j < EPL; ++j) {
+            const E ev = ep[c * 16 + j];
+            const uint32_t o = eoff(ev) >> C::OSH;
+            PFma<TX, TW, C::EPV>::run(acc, *reinterpret_cast<const uint4*>(x0 + o), eval(ev));
+            if constexpr (C::VPL == 2)
+              PFma<TX, TW, C::EPV>::run(acc + C::EPV, *reinterpret_cast<const uint4*>(x1 + o), eval(ev));
+          }
         }
       } else if constexpr (C::W16) {
         const uint4* ep = reinterpret_cast<const uint4*>(ebuf(buf) + (off - base) * 4) + gq;
@@ -553,19 +579,34 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
       const int tile = h.work / P.nblocks, b = h.work % P.nblocks;
       const int64_t row = (int64_t)b * kRowsPerBlock + rb;
       float* yt = P.y + (size_t)tile * P.nrows * ST;
-      if constexpr (C::ES > 1) {
+      if constexpr (C::SWZ) {
+        // the two lanes of a row hold the same slices in swapped halves:
+        // each adds the partner's partial sums of both halves
+#pragma unroll
+        for (int i = 0; i < C::EPV; ++i) {
+          const float t0 = __shfl_xor_sync(0xffffffffu, acc[C::EPV + i], C::LPR);
+          const float t1 = __shfl_xor_sync(0xffffffffu, acc[i], C::LPR);
+          acc[i] += t0;
+          acc[C::EPV + i] += t1;
+        }
+      } else if constexpr (C::ES > 1) {
         // the row's partial sums of the ES lanes (fixed order: a butterfly)
 #pragma unroll
         for (int o = C::LPR; o < C::LPR * C::ES; o <<= 1)
 #pragma unroll
           for (int i = 0; i < C::SPL; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
       }
+      // accumulator group v holds the slices of row half hv (with the swap,
+      // group 0 is the lane's own half; only that one is written and summed)
+      constexpr int VOWN = C::SWZ ? 1 : C::VPL;
+      const bool writer = C::SWZ || el == 0;
       float r[C::SPL];
 #pragma unroll
       for (int v = 0; v < C::VPL; ++v)
 #pragma unroll
         for (int e = 0; e < C::EPV; ++e) {
-          const int sl = v * C::LPR * C::EPV + sub * C::EPV + e;
+          const int hv = C::SWZ ? (v ^ el) : v;
+          const int sl = hv * C::LPR * C::EPV + sub * C::EPV + e;
           float scale = 1.0f;
           if constexpr (C::X16)
             scale = ldexpf(1.0f, ceil_log2_exp_p(__uint_as_float(__ldg(P.in_max + tile * ST + sl))) -
@@ -574,10 +615,11 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
             scale = ldexpf(1.0f, -P.mat_scale_exp);
           r[v * C::EPV + e] = acc[v * C::EPV + e] * scale;
         }
-      if (row < P.nrows && el == 0) {
+      if (row < P.nrows && writer) {
 #pragma unroll
-        for (int v = 0; v < C::VPL; ++v) {
-          float* dst = yt + (size_t)row * ST + v * C::LPR * C::EPV + sub * C::EPV;
+        for (int v = 0; v < VOWN; ++v) {
+          const int hv = C::SWZ ? (v ^ el) : v;
+          float* dst = yt + (size_t)row * ST + hv * C::LPR * C::EPV + sub * C::EPV;
 #pragma unroll
           for (int q = 0; q < C::EPV / 4; ++q)
             reinterpret_cast<float4*>(dst)[q] =
@@ -589,13 +631,14 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
         // per-slice squared norm of the block's rows: lanes sharing `sub`
         // hold the same slices (reduce over rows by shuffles), then the 16
         // consumer warps combine through shared memory in a fixed order
-        double d[C::SPL];
+        constexpr int DN = VOWN * C::EPV;
+        double d[DN];
 #pragma unroll
-        for (int i = 0; i < C::SPL; ++i) d[i] = (double)r[i] * (double)r[i];
+        for (int i = 0; i < DN; ++i) d[i] = (double)r[i] * (double)r[i];
 #pragma unroll
         for (int o = C::LPR * C::ES; o < 32; o <<= 1)
 #pragma unroll
-          for (int i = 0; i < C::SPL; ++i) d[i] += __shfl_xor_sync(0xffffffffu, d[i], o);
+          for (int i = 0; i < DN; ++i) d[i] += __shfl_xor_sync(0xffffffffu, d[i], o);
         // the staged rows of this buffer are no longer read once every
         // consumer warp is here: their area holds the [NC][ST] partials
         // (the buffer is released only after the reduction)
@@ -608,12 +651,14 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
           if (lane == 0) atomicExch(a.err, 1);
           return;
         }
-        if (rw == 0 && el == 0) {
+        if (rw == 0 && writer) {
 #pragma unroll
-          for (int v = 0; v < C::VPL; ++v)
+          for (int v = 0; v < VOWN; ++v) {
+            const int hv = C::SWZ ? (v ^ el) : v;
 #pragma unroll
             for (int e = 0; e < C::EPV; ++e)
-              red[warp * ST + v * C::LPR * C::EPV + sub * C::EPV + e] = d[v * C::EPV + e];
+              red[warp * ST + hv * C::LPR * C::EPV + sub * C::EPV + e] = d[v * C::EPV + e];
+          }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&redbar[1]);
