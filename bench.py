@@ -621,6 +621,8 @@ def run_ours(args):
     accuracy = _accuracy(xct, plans, p64, w, first, count, per_rank * world, S, n, K, y, y64,
                          err_vs_phantom, stream, dev)
     hbm_regime = _hbm_regime(xct, plans["f16"], y, n, m, nd, nnz, _peaks()[0], stream)
+    with xct.Plan(n, m, nd, "f16", cos_sin=w["cos_sin"], few_slices=True) as pw:
+        hbm_regime_wide = _hbm_regime(xct, pw, y, n, m, nd, nnz, _peaks()[0], stream)
 
     if rank != 0:
         return
@@ -686,7 +688,10 @@ def run_ours(args):
         "vs_fp64": vs64,
         "accuracy_vs_fp64": accuracy,
         "hbm_regime": {"storage": "f16", "note": "few slices: the packed matrix stream (nnz x 4 B) "
-                       "sets the roof; slice counts below 8 run as an 8-slice tile", "by_slices": hbm_regime,
+                       "sets the roof; slice counts below 8 run as an 8-slice tile; by_slices: the "
+                       "plan's own layouts, by_slices_wide: a plan built with XCT_PLAN_FEW_SLICES "
+                       "(wide stages, entries streamed from device memory)", "by_slices": hbm_regime,
+                       "by_slices_wide": hbm_regime_wide,
                        "peak_gbs": _peaks()[0], "peak_source": _peaks()[1]},
         "rel_err_projection_vs_fp64": proj_err64,
         "graph_ms_per_step": graph_ms,
@@ -767,7 +772,7 @@ def run_products(args):
     wl = inputs.WORKLOADS[WORKLOAD]
     n, m, nd = wl["n"], wl["m"], wl["nd"]
     S = args.slices or wl["slices"]
-    plan = xct.Plan(n, m, nd, args.storage, cos_sin=inputs.angle_table(m))
+    plan = xct.Plan(n, m, nd, args.storage, cos_sin=inputs.angle_table(m), few_slices=args.few_slices)
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.rand((S, n, n), device="cuda", generator=g)
     y = torch.rand((S, m, nd), device="cuda", generator=g)
@@ -789,6 +794,7 @@ def run_products(args):
     tp, tb = e[0].elapsed_time(e[1]) / args.steps, e[1].elapsed_time(e[2]) / args.steps
     st = plan.stats()
     print(json.dumps({"mode": "products", "storage": args.storage, "nnz": nnz, "slices": S,
+                      "few_slices": args.few_slices,
                       "stages_a": st["stages_a"], "stages_at": st["stages_at"],
                       "slots_a": st["slots_a"], "slots_at": st["slots_at"],
                       "bytes_a": st["bytes_a"], "bytes_at": st["bytes_at"],
@@ -1203,6 +1209,8 @@ def main():
     ap.add_argument("--storage", default="f16", choices=["f32", "f16", "bf16", "f16a", "bf16a"])
     ap.add_argument("--slices", type=int, default=0,
                     help="--mode products: slices per product (default: the workload's 64)")
+    ap.add_argument("--few-slices", action="store_true",
+                    help="--mode products: build the plan with XCT_PLAN_FEW_SLICES (wide-stage layouts)")
     args = ap.parse_args()
     if args.mode == "products":
         run_products(args)

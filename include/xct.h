@@ -93,6 +93,15 @@ typedef struct xct_plan_s* xct_plan_t;
                                  pixels (of A) or rays (of A^T) a CTA stages at
                                  a time -- by timing its product on the widest
                                  slice tile (about 3x the layout time) */
+#define XCT_PLAN_FEW_SLICES 4u  /* XCT_F16 / XCT_BF16 only: also build
+                                   wide-stage layouts of A and A^T (stages of
+                                   up to 1016 staged rows, the packed entries
+                                   read straight from device memory) for
+                                   products of at most 8 slices, where the
+                                   matrix stream from HBM is the lowest roof
+                                   (Sec. III-B, roofline: input buffering of
+                                   many columns per stage); about doubles the
+                                   plan's memory and build time */
 
 /*
  * xct_plan -- build the memoized operator (Sec. II-B memoization; Sec. III-A1

@@ -611,8 +611,12 @@ xct_status xct_plan(const xct_geometry* g, xct_dtype storage, uint32_t flags, vo
     set_error("storage %d is not XCT_F32, XCT_F16, XCT_BF16, XCT_F16A or XCT_BF16A", (int)storage);
     return XCT_ERR_INVALID;
   }
-  if (flags & ~(XCT_PLAN_KEEP_F64 | XCT_PLAN_AUTOTUNE)) {
+  if (flags & ~(XCT_PLAN_KEEP_F64 | XCT_PLAN_AUTOTUNE | XCT_PLAN_FEW_SLICES)) {
     set_error("unknown plan flags 0x%x", flags);
+    return XCT_ERR_INVALID;
+  }
+  if ((flags & XCT_PLAN_FEW_SLICES) && !stages16(storage)) {
+    set_error("XCT_PLAN_FEW_SLICES needs XCT_F16 or XCT_BF16 storage");
     return XCT_ERR_INVALID;
   }
   std::unique_ptr<xct_plan_s> p(new xct_plan_s());

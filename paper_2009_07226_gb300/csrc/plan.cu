@@ -731,11 +731,12 @@ __global__ void run_fill_kernel(const int64_t* blk_stage, const int64_t* fp_off,
   }
 }
 
-// per (stage, quad): the 4 row counts and the padded slot count
+// per (stage, quad): the 4 row counts and the padded slot count (the
+// quad's longest row rounded up to `per_row` entries, for each of 4 rows)
 __global__ void __launch_bounds__(kRowsPerBlock) seg_count_kernel(CsrView m, const int32_t* epos,
                                                                   const int64_t* blk_stage,
-                                                                  int32_t cap, Seg* seg,
-                                                                  int64_t* slots) {
+                                                                  int32_t cap, int32_t per_row,
+                                                                  Seg* seg, int64_t* slots) {
   __shared__ uint16_t cnt[kRowsPerBlock][kStageChunk + 2];  // counts <= capacity
   const int b = blockIdx.x;
   const int64_t sb = blk_stage[b], ns = blk_stage[b + 1] - sb;
@@ -763,7 +764,7 @@ __global__ void __launch_bounds__(kRowsPerBlock) seg_count_kernel(CsrView m, con
       sg.off = 0;
       int64_t gi = (sb + s0 + st) * kQuads + q;
       seg[gi] = sg;
-      slots[gi] = (int64_t)((mx + 3) / 4) * 16;
+      slots[gi] = (int64_t)((mx + per_row - 1) / per_row) * per_row * 4;
     }
     __syncthreads();
   }
@@ -810,8 +811,8 @@ __global__ void desc_fill_kernel(const int64_t* stage_ent, const int32_t* stage_
 }
 
 template <int EB>
-__global__ void pad_fill_kernel(void* ent, int64_t nslots, uint32_t zero_slot) {
-  const uint32_t off = zero_slot * (uint32_t)kEntryRowBytes;
+__global__ void pad_fill_kernel(void* ent, int64_t nslots, uint32_t zero_slot, uint32_t unit) {
+  const uint32_t off = zero_slot * unit;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nslots;
        i += (int64_t)gridDim.x * blockDim.x) {
     if (EB == 4)
@@ -822,8 +823,9 @@ __global__ void pad_fill_kernel(void* ent, int64_t nslots, uint32_t zero_slot) {
 }
 
 template <int KIND>  // 0: f32, 1: f16 (x 2^15), 2: bf16
-__device__ __forceinline__ void pack_entry(void* ent, int64_t slot, uint32_t local, double v) {
-  const uint32_t off = local * (uint32_t)kEntryRowBytes;
+__device__ __forceinline__ void pack_entry(void* ent, int64_t slot, uint32_t local, double v,
+                                           uint32_t unit) {
+  const uint32_t off = local * unit;
   if (KIND == 0) {
     unsigned long long w = (unsigned long long)off |
                            ((unsigned long long)__float_as_uint(__double2float_rn(v)) << 32);
@@ -841,7 +843,7 @@ template <int KIND>
 __global__ void __launch_bounds__(kRowsPerBlock) fill_entries_kernel(CsrView m, const int32_t* epos,
                                                                      const int64_t* blk_stage,
                                                                      int32_t cap, const Seg* seg,
-                                                                     void* ent) {
+                                                                     void* ent, uint32_t unit) {
   __shared__ uint16_t cnt[kRowsPerBlock][kStageChunk + 2];  // counts <= capacity
   const int b = blockIdx.x;
   const int64_t sb = blk_stage[b], ns = blk_stage[b + 1] - sb;
@@ -858,16 +860,101 @@ __global__ void __launch_bounds__(kRowsPerBlock) fill_entries_kernel(CsrView m, 
       int32_t k = cnt[threadIdx.x][st];
       cnt[threadIdx.x][st] = (uint16_t)(k + 1);
       int64_t slot = seg[(sb + s0 + st) * kQuads + q].off + (k >> 2) * 16 + g * 4 + (k & 3);
-      pack_entry<KIND>(ent, slot, (uint32_t)(p % cap), m.val[e]);
+      pack_entry<KIND>(ent, slot, (uint32_t)(p % cap), m.val[e], unit);
     }
   }
 }
 
+// Entry order of a wide-stage layout (16-byte staged rows, 16-bit entries).
+// The product kernel's four lanes of a row read, at one time step, slot q of
+// chunks 4i .. 4i + 3 (lane e takes chunk 4i + e), and the lanes of the two
+// rows g = 2h, 2h + 1 of a quad issue their loads together (one phase of 8
+// lanes of a 16-byte load).
+//  - Placement: a quad's chunks lie in groups of 4 per row, one group of all
+//    4 rows after the other (chunk c of row g at 16-byte chunk
+//    (c / 4) * 16 + g * 4 + c % 4; the segment holds the quad's longest row
+//    rounded up to 16 entries for each row), so the 8 lanes of a phase read
+//    128 contiguous bytes of entries.
+//  - Order: staged row j lies in shared-memory bank group j mod 8, so two of
+//    a phase's 8 reads of staged rows conflict when their rows differ and
+//    share the group.  The order of a row's entries is free (the row's sum
+//    is the same up to the rounding of its FP32 accumulation), so this pass
+//    takes each half quad's entries one time step at a time, giving the 8
+//    reads distinct groups where the remaining entries allow: for each lane
+//    an entry of the free group with the most entries left in its row, else
+//    a padding entry (the zero slot; several of them in a phase read one
+//    address), else an entry of the row's largest group.
+// `src` is a copy of the entries in the CSR-order placement of
+// fill_entries_kernel, `ent` starts as padding; one thread per half quad.
+__global__ void wide_order_kernel(const uint32_t* src, uint32_t* ent, const Seg* seg,
+                                  int64_t nhalf, uint32_t zero_entry) {
+  const int zg = (int)((zero_entry >> 20) & 7u);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nhalf;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const Seg sg = seg[t >> 1];
+    const int h = (int)(t & 1);
+    int cnt[2], nch[2], pads[2];
+    int left[2][8], scan[2][8];
+    for (int r = 0; r < 2; ++r) {
+      cnt[r] = sg.cnt[2 * h + r];
+      nch[r] = (cnt[r] + 3) >> 2;
+      pads[r] = 4 * nch[r] - cnt[r];
+      for (int b = 0; b < 8; ++b) left[r][b] = 0, scan[r][b] = 0;
+    }
+    auto slot = [&](int r, int k) { return sg.off + (k >> 2) * 16 + (2 * h + r) * 4 + (k & 3); };
+    for (int r = 0; r < 2; ++r)
+      for (int k = 0; k < cnt[r]; ++k) ++left[r][(src[slot(r, k)] >> 20) & 7u];
+    const int nmax = nch[0] > nch[1] ? nch[0] : nch[1];
+    for (int i = 0; 4 * i < nmax; ++i)
+      for (int q = 0; q < 4; ++q) {
+        uint32_t used = 0;     // groups taken by matrix entries at this step
+        bool pad_here = false;
+        for (int e = 0; e < 4; ++e)
+          for (int r = 0; r < 2; ++r) {
+            const int c = 4 * i + e;
+            if (c >= nch[r]) continue;
+            int best = -1;
+            for (int b = 0; b < 8; ++b)
+              if (left[r][b] > 0 && !((used >> b) & 1u) && !(pad_here && b == zg) &&
+                  (best < 0 || left[r][b] > left[r][best]))
+                best = b;
+            uint32_t v;
+            if (best < 0 && pads[r] > 0 && !((used >> zg) & 1u)) {
+              v = zero_entry;
+              --pads[r];
+              pad_here = true;
+            } else {
+              if (best < 0)
+                for (int b = 0; b < 8; ++b)
+                  if (left[r][b] > 0 && (best < 0 || left[r][b] > left[r][best])) best = b;
+              if (best < 0) {   // only padding left in this row
+                v = zero_entry;
+                --pads[r];
+                pad_here = true;
+              } else {
+                int k = scan[r][best];   // an entry of group `best` lies at or after k
+                while (k < cnt[r] - 1 && ((src[slot(r, k)] >> 20) & 7u) != (uint32_t)best) ++k;
+                v = src[slot(r, k)];
+                scan[r][best] = k + 1;
+                --left[r][best];
+                used |= 1u << best;
+              }
+            }
+            const int g = 2 * h + r;
+            ent[sg.off + ((int64_t)i * 16 + g * 4 + e) * 4 + q] = v;
+          }
+      }
+  }
+}
+
 xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_t cap, Layout& L,
-                        Arena& keep, cudaStream_t s) {
+                        Arena& keep, cudaStream_t s, int gap = -1,
+                        int32_t unit = kEntryRowBytes) {
+  if (gap < 0) gap = gap_fill_for(storage);
   L.nrows = m.nrows;
   L.ncols = m.ncols;
   L.cap = cap;
+  L.unit = unit;
   L.ebytes = storage == XCT_F32 ? 8 : 4;
   L.nblocks = (int32_t)((m.nrows + kRowsPerBlock - 1) / kRowsPerBlock);
   const int32_t nb = L.nblocks;
@@ -886,7 +973,7 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
   XCT_TRY_CUDA(cudaFuncSetAttribute(fp_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)fill_smem));
   if (nb > 0) {
-    fp_count_kernel<<<nb, kFpThreads, bm_smem, s>>>(m, gap_fill_for(storage), fp_size);
+    fp_count_kernel<<<nb, kFpThreads, bm_smem, s>>>(m, gap, fp_size);
     count_launch();
   }
   if (nb > 0) {
@@ -903,7 +990,7 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
   XCT_TRY_CUDA(cudaMemsetAsync(L.pix, 0, sizeof(int32_t) * (total_fp + 4), s));
   XCT_TRY(own.get(&L.blk_stage, nb + 1));
   if (nb > 0) {
-    fp_fill_kernel<<<nb, kFpThreads, fill_smem, s>>>(m, gap_fill_for(storage), fp_off, L.pix, epos);
+    fp_fill_kernel<<<nb, kFpThreads, fill_smem, s>>>(m, gap, fp_off, L.pix, epos);
     stage_count_kernel<<<grid_for(nb, 256), 256, 0, s>>>(fp_size, nb, cap, nst);
     count_launch(2);
   }
@@ -952,7 +1039,9 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
     }
   }
   if (nb > 0) {
-    seg_count_kernel<<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, slots);
+    // wide-stage layouts: groups of 4 chunks per row (see wide_order_kernel)
+    seg_count_kernel<<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap,
+                                                  unit == kWideRowBytes ? 16 : 4, L.seg, slots);
     count_launch();
   }
   XCT_TRY(exclusive_scan_i64(slots, slot_off, L.nstages * kQuads, s));
@@ -977,21 +1066,38 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
     unsigned long long* e;
     XCT_TRY(own.get(&e, L.nslots));
     L.ent = e;
-    pad_fill_kernel<8><<<grid_for(L.nslots, 256, 152 * 32), 256, 0, s>>>(L.ent, L.nslots, (uint32_t)cap);
+    pad_fill_kernel<8><<<grid_for(L.nslots, 256, 152 * 32), 256, 0, s>>>(L.ent, L.nslots, (uint32_t)cap,
+                                                                         (uint32_t)unit);
   } else {
     uint32_t* e;
     XCT_TRY(own.get(&e, L.nslots));
     L.ent = e;
-    pad_fill_kernel<4><<<grid_for(L.nslots, 256, 152 * 32), 256, 0, s>>>(L.ent, L.nslots, (uint32_t)cap);
+    pad_fill_kernel<4><<<grid_for(L.nslots, 256, 152 * 32), 256, 0, s>>>(L.ent, L.nslots, (uint32_t)cap,
+                                                                         (uint32_t)unit);
   }
   count_launch();
   if (nb > 0) {
     if (storage == XCT_F32)
-      fill_entries_kernel<0><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent);
+      fill_entries_kernel<0><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent,
+                                                            (uint32_t)unit);
     else if (half_values(storage))
-      fill_entries_kernel<1><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent);
+      fill_entries_kernel<1><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent,
+                                                            (uint32_t)unit);
     else
-      fill_entries_kernel<2><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent);
+      fill_entries_kernel<2><<<nb, kRowsPerBlock, 0, s>>>(m, epos, L.blk_stage, cap, L.seg, L.ent,
+                                                            (uint32_t)unit);
+    count_launch();
+  }
+  if (unit == kWideRowBytes && L.ebytes == 4 && L.nslots > 0) {
+    uint32_t* src;
+    XCT_TRY(tmp.get(&src, L.nslots));
+    XCT_TRY_CUDA(cudaMemcpyAsync(src, L.ent, sizeof(uint32_t) * L.nslots, cudaMemcpyDeviceToDevice, s));
+    pad_fill_kernel<4><<<grid_for(L.nslots, 256, 152 * 32), 256, 0, s>>>(L.ent, L.nslots, (uint32_t)cap,
+                                                                         (uint32_t)unit);
+    count_launch();
+    const int64_t nhalf = L.nstages * kQuads * 2;
+    wide_order_kernel<<<grid_for(nhalf, 128), 128, 0, s>>>(src, static_cast<uint32_t*>(L.ent), L.seg,
+                                                           nhalf, ((uint32_t)cap * unit) << 16);
     count_launch();
   }
   // stage descriptors: run lists padded to an even count of at least 2
@@ -1287,6 +1393,20 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
     best_mem.move_to(keep);
   }
   const int32_t cap_used = p.la.cap;
+  // wide-stage layouts for products of few slices (16-byte staged rows):
+  // stages of up to kWideCap rows, gaps of up to kWideGap unreferenced rows
+  // filled, offsets at 16 bytes per row; the entries stay in global memory
+  if (p.flags & XCT_PLAN_FEW_SLICES) {
+    for (int which = 0; which < 2; ++which) {
+      Arena mem(s);
+      Layout& out = which == 0 ? p.law : p.latw;
+      XCT_TRY(build_layout(which == 0 ? ma : mt, p.nnz, p.storage, kWideCap, out, mem, s, kWideGap,
+                           kWideRowBytes));
+      mem.move_to(keep);
+    }
+    p.la.wide = &p.law;
+    p.lat.wide = &p.latw;
+  }
 
   if (p.flags & XCT_PLAN_KEEP_F64) {
     p.a_rowptr = rowptr; p.a_col = col; p.a_val = val;
@@ -1420,8 +1540,8 @@ xct_status export_matrix(Plan& p, int what, int64_t* rowptr, int32_t* col, doubl
                 memcpy(&ff, &f, 4);
                 v = ff;
               }
-              idx = off / kEntryRowBytes;
-              if (off % kEntryRowBytes || idx >= (uint32_t)(sp[st + 1] - sp[st]) || row >= nrows) {
+              idx = off / (uint32_t)L.unit;
+              if (off % (uint32_t)L.unit || idx >= (uint32_t)(sp[st + 1] - sp[st]) || row >= nrows) {
                 set_error("packed layout holds an out-of-range entry (block %d stage %lld)", b,
                           (long long)st);
                 return XCT_ERR_CUDA;

@@ -466,10 +466,12 @@ xct_status spmm_stage(const SpmmArgs& a, cudaStream_t s) {
   return a.storage == XCT_F16 ? stage16<__half>(a, s) : stage16<__nv_bfloat16>(a, s);
 }
 
-xct_status spmm_run(const SpmmArgs& a, cudaStream_t s) {
-  if (a.L->cap > kMaxStageCap) {
+xct_status spmm_run(const SpmmArgs& a0, cudaStream_t s) {
+  const SpmmArgs a = on_product_layout(a0);
+  const int max_cap = 65535 / a.L->unit - 1;   // the zero slot's offset fits 16 bits
+  if (a.L->cap > max_cap) {
     set_error("stage capacity %d exceeds the 16-bit staged-row offset (at most %d)", a.L->cap,
-              kMaxStageCap);
+              max_cap);
     return XCT_ERR_UNSUPPORTED;
   }
   if (!valid_storage(a.storage)) {
@@ -477,6 +479,10 @@ xct_status spmm_run(const SpmmArgs& a, cudaStream_t s) {
     return XCT_ERR_INVALID;
   }
   if (spmm_pipe_applies(a)) return spmm_pipe(a, s);
+  if (a.L->unit != kEntryRowBytes) {
+    set_error("wide-stage layout without a fitting persistent product");
+    return XCT_ERR_UNSUPPORTED;
+  }
   if (matrix16(a.storage) && !stages16(a.storage)) {
     set_error("16-bit matrix with FP32 vectors needs the persistent product (tile width %d, "
               "stage capacity %d)", a.st, a.L->cap);

@@ -114,6 +114,12 @@ constexpr int kQuads = kRowsPerBlock / 4;      // 4-row groups per block
 // in 16 bits.
 constexpr int kEntryRowBytes = 128;
 constexpr int kMaxStageCap = 65535 / kEntryRowBytes - 1;
+// wide-stage layouts for few slices: 16-byte rows addressed at 16 bytes per
+// row (up to 4094 rows a stage), entries streamed from global memory by the
+// consumers instead of staged
+constexpr int kWideRowBytes = 16;
+constexpr int kWideCap = 1016;
+constexpr int kWideGap = 16;
 // log2(128 / pixb) for staged rows of pixb = 2 .. 128 bytes
 __host__ __device__ constexpr int entry_shift(int pixb) {
   return pixb >= 128 ? 0 : pixb == 64 ? 1 : pixb == 32 ? 2 : pixb == 16 ? 3 : pixb == 8 ? 4
@@ -165,6 +171,12 @@ struct Layout {
   int64_t run_max = 0;            // largest stage list, in pairs
   unsigned char* desc = nullptr;  // [nstages] stage descriptors of desc_bytes each
   int64_t desc_bytes = 0;
+  // bytes per staged row in the entries' offsets (kEntryRowBytes, or 16 for
+  // a wide-stage layout whose offsets address 16-byte rows directly)
+  int32_t unit = kEntryRowBytes;
+  // the wide-stage layout of the same matrix for 16-byte staged rows (built
+  // with XCT_PLAN_FEW_SLICES), used in place of this one for such tiles
+  const Layout* wide = nullptr;
   int64_t bytes = 0;
 };
 
@@ -215,6 +227,7 @@ struct Plan {
   int32_t* ray_order = nullptr;
   int32_t* ray_inv = nullptr;
   Layout la, lat;
+  Layout law, latw;              // wide-stage layouts (XCT_PLAN_FEW_SLICES)
   int32_t mat_scale_exp = 0;     // k: stored value = RN(l * 2^k)
   int* err = nullptr;            // device flag: a bounded wait in a kernel ran out
   // kept FP64 matrices (ordered ids), only with XCT_PLAN_KEEP_F64
@@ -267,6 +280,12 @@ struct SpmmArgs {
   int* work;               // scratch: one work counter (persistent form)
   int* err;                // device flag set to 1 if a bounded wait ran out
 };
+// The layout a product runs on: the matrix's wide-stage layout, where the
+// plan built one, for 16-byte staged rows of 16-bit slices; else its own.
+inline SpmmArgs on_product_layout(SpmmArgs a) {
+  if (a.L->wide && stages16(a.storage) && a.st * 2 == kWideRowBytes) a.L = a.L->wide;
+  return a;
+}
 xct_status spmm(const SpmmArgs& a, cudaStream_t s);   // = spmm_stage + spmm_run
 // 16-bit storage: the normalised 16-bit copy of the input (no-op for FP32)
 xct_status spmm_stage(const SpmmArgs& a, cudaStream_t s);
