@@ -263,6 +263,39 @@ __device__ __forceinline__ int ceil_log2_exp_p(float m) {
   return f == 0.5f ? ex - 1 : ex;
 }
 
+// Sum over the rows of a warp of N FP64 values per lane, lanes paired over
+// lane bits O, 2 O, .. 16: while a lane holds more than one value, the pair
+// splits them (the lane with bit O clear keeps the first half, its partner
+// the second; each adds the partner's value of the same slice), so every
+// addition is done once; a single value goes through the plain butterfly.
+// Each slice's sum is the same tree of additions as the plain butterfly.
+// `base` returns the index (among the lane's N) of its first kept value.
+template <int N, int O>
+__device__ __forceinline__ void halve_rows(double* d, int lane, int& base) {
+  if constexpr (O < 32) {
+    if constexpr (N > 1) {
+      const bool up = (lane & O) != 0;
+#pragma unroll
+      for (int i = 0; i < N / 2; ++i) {
+        const double send = up ? d[i] : d[N / 2 + i];
+        const double keep = up ? d[N / 2 + i] : d[i];
+        d[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+      }
+      if (up) base += N / 2;
+      halve_rows<N / 2, 2 * O>(d, lane, base);
+    } else {
+      d[0] += __shfl_xor_sync(0xffffffffu, d[0], O);
+      halve_rows<1, 2 * O>(d, lane, base);
+    }
+  }
+}
+// values a lane holds after halve_rows<N, O>, and the lane bits over which
+// lanes then hold duplicates (the plain butterfly's levels)
+__host__ __device__ constexpr int halved_count(int n, int o) { return o >= 32 ? n : halved_count(n > 1 ? n / 2 : 1, 2 * o); }
+__host__ __device__ constexpr int halved_dup_mask(int n, int o) {
+  return o >= 32 ? 0 : (n > 1 ? halved_dup_mask(n / 2, 2 * o) : (o | halved_dup_mask(1, 2 * o)));
+}
+
 template <class TX, class TW, int ST, bool WIDE>
 __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
     spmm_pipe_kernel(PipeArgs a) {
@@ -669,15 +702,27 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
       if (P.dot) {
         // per-slice squared norm of the block's rows: lanes sharing `sub`
         // hold the same slices (reduce over rows by shuffles), then the 16
-        // consumer warps combine through shared memory in a fixed order
-        constexpr int DN = VOWN * C::EPV;
+        // consumer warps combine through shared memory in a fixed order.
+        // FP64 arithmetic is slow on this part (1/64 of the FP32 rate), so
+        // none of it is repeated: with lanes splitting a row's entries
+        // (16-byte rows), the ES lanes of a row hold the same sums after the
+        // butterfly above and each squares EPV / ES of the slices; the sum
+        // over rows splits the values between paired lanes (halve_rows)
+        constexpr bool SPLIT = C::ES > 1 && !C::SWZ && C::VPL == 1 && C::LPR == 1;
+        constexpr int DN = SPLIT ? C::EPV / C::ES : VOWN * C::EPV;
         double d[DN];
+        if constexpr (SPLIT) {
 #pragma unroll
-        for (int i = 0; i < DN; ++i) d[i] = (double)r[i] * (double)r[i];
+          for (int e = 0; e < C::EPV; ++e)
+            if (e / DN == el) d[e % DN] = (double)r[e] * (double)r[e];
+        } else {
 #pragma unroll
-        for (int o = C::LPR * C::ES; o < 32; o <<= 1)
-#pragma unroll
-          for (int i = 0; i < DN; ++i) d[i] += __shfl_xor_sync(0xffffffffu, d[i], o);
+          for (int i = 0; i < DN; ++i) d[i] = (double)r[i] * (double)r[i];
+        }
+        int base = 0;
+        halve_rows<DN, C::LPR * C::ES>(d, lane, base);
+        constexpr int NF = halved_count(DN, C::LPR * C::ES);
+        constexpr int DUP = halved_dup_mask(DN, C::LPR * C::ES);
         // the staged rows of this buffer are no longer read once every
         // consumer warp is here: their area holds the [NC][ST] partials
         // (the buffer is released only after the reduction)
@@ -690,13 +735,19 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
           if (lane == 0) atomicExch(a.err, 1);
           return;
         }
-        if (rw == 0 && writer) {
+        if ((lane & DUP) == 0) {
 #pragma unroll
-          for (int v = 0; v < VOWN; ++v) {
-            const int hv = C::SWZ ? (v ^ el) : v;
-#pragma unroll
-            for (int e = 0; e < C::EPV; ++e)
-              red[warp * ST + hv * C::LPR * C::EPV + sub * C::EPV + e] = d[v * C::EPV + e];
+          for (int i = 0; i < NF; ++i) {
+            const int j = base + i;   // index among the lane's DN squares
+            int sl;
+            if constexpr (SPLIT) {
+              sl = el * DN + j;
+            } else {
+              const int v = j / C::EPV, e = j % C::EPV;
+              const int hv = C::SWZ ? (v ^ el) : v;
+              sl = hv * C::LPR * C::EPV + sub * C::EPV + e;
+            }
+            red[warp * ST + sl] = d[i];
           }
         }
         __syncwarp();
