@@ -263,28 +263,54 @@ __device__ __forceinline__ int ceil_log2_exp_p(float m) {
   return f == 0.5f ? ex - 1 : ex;
 }
 
-// Sum over the rows of a warp of N FP64 values per lane, lanes paired over
-// lane bits O, 2 O, .. 16: while a lane holds more than one value, the pair
-// splits them (the lane with bit O clear keeps the first half, its partner
-// the second; each adds the partner's value of the same slice), so every
-// addition is done once; a single value goes through the plain butterfly.
-// Each slice's sum is the same tree of additions as the plain butterfly.
+// An unevaluated sum h + l of two FP32 values: squares of FP32 values are
+// exact in it (l from an FMA), and sums of such non-negative terms keep
+// about 47 bits (two-sum of the high parts, then renormalisation), on the
+// FP32 pipes.
+struct Ff {
+  float h, l;
+};
+__device__ __forceinline__ Ff ff_square(float r) {
+  const float h = __fmul_rn(r, r);
+  return {h, __fmaf_rn(r, r, -h)};
+}
+__device__ __forceinline__ Ff sum2(Ff a, Ff b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float v = __fsub_rn(s, a.h);
+  const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, v)), __fsub_rn(b.h, v));   // s's error, exact
+  const float t = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  const float h = __fadd_rn(s, t);
+  return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ double sum2(double a, double b) { return a + b; }
+__device__ __forceinline__ Ff shfl_xor(Ff v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+}
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+
+// Sum over the rows of a warp of N values per lane (FP64 or Ff), lanes
+// paired over lane bits O, 2 O, .. 16: while a lane holds more than one
+// value, the pair splits them (the lane with bit O clear keeps the first
+// half, its partner the second; each adds the partner's value of the same
+// slice), so every addition is done once; a single value goes through the
+// plain butterfly.  Each slice's sum is the same tree of additions as the
+// plain butterfly (both additions are commutative bit for bit).
 // `base` returns the index (among the lane's N) of its first kept value.
-template <int N, int O>
-__device__ __forceinline__ void halve_rows(double* d, int lane, int& base) {
+template <int N, int O, class T>
+__device__ __forceinline__ void halve_rows(T* d, int lane, int& base) {
   if constexpr (O < 32) {
     if constexpr (N > 1) {
       const bool up = (lane & O) != 0;
 #pragma unroll
       for (int i = 0; i < N / 2; ++i) {
-        const double send = up ? d[i] : d[N / 2 + i];
-        const double keep = up ? d[N / 2 + i] : d[i];
-        d[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+        const T send = up ? d[i] : d[N / 2 + i];
+        const T keep = up ? d[N / 2 + i] : d[i];
+        d[i] = sum2(keep, shfl_xor(send, O));
       }
       if (up) base += N / 2;
       halve_rows<N / 2, 2 * O>(d, lane, base);
     } else {
-      d[0] += __shfl_xor_sync(0xffffffffu, d[0], O);
+      d[0] = sum2(d[0], shfl_xor(d[0], O));
       halve_rows<1, 2 * O>(d, lane, base);
     }
   }
@@ -311,6 +337,10 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
   uint64_t* dbar = full + 2 * NB;        // descriptor of a stage landed
   uint64_t* redbar = full + 2 * NB + DS;  // consumers' rendezvous at a block end (2)
   int4* ident = reinterpret_cast<int4*>(redbar + 2);
+  // 16-byte rows of 16-bit slices: [NB][NC][ST] block-end partials (FP32
+  // pairs) and [NB] counters of the warps past a block end
+  float2* dpair = reinterpret_cast<float2*>(ident + DS);
+  int* dcnt = reinterpret_cast<int*>(dpair + (C::PIXB == 16 && C::X16 ? NB * C::NC * ST : 0));
   auto dslot = [&](int k) { return dslots + (size_t)k * a.dbytes; };
   auto xbuf = [&](int b) { return smem + b * bufbytes; };
   auto ebuf = [&](int b) { return smem + b * bufbytes + a.xbytes; };
@@ -326,6 +356,8 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
     for (int k = 0; k < kDescSlots; ++k) mbar_init(&dbar[k], 1);
     mbar_init(&redbar[0], C::NC);
     mbar_init(&redbar[1], C::NC);
+    if constexpr (C::PIXB == 16 && C::X16)
+      for (int b = 0; b < NB; ++b) dcnt[b] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // zero slot of each product (row `cap` of its layout) in every buffer:
@@ -699,7 +731,58 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
                             r[v * C::EPV + 4 * q + 2], r[v * C::EPV + 4 * q + 3]);
         }
       }
-      if (P.dot) {
+      if constexpr (C::PIXB == 16 && C::X16) {
+        if (P.dot) {
+          // per-slice squared norm of the block's rows, for 16-byte rows of
+          // 16-bit slices: the row sums before the de-normalisation are
+          // bounded (normalised inputs times 16-bit matrix values), so their
+          // squares and sums are FP32 pairs (Ff), scaled by the slice's
+          // power of two squared when converted to FP64.  The four lanes of
+          // a row hold the same sums: each squares two of the 8 slices, the
+          // sum over the warp's rows halves them between paired lanes.  The
+          // warp's pairs go to this buffer's [NC][ST] area; the last warp
+          // past the block end adds them in warp order and writes the
+          // partials, and no warp waits for the others.  The area and its
+          // counter are used again only at a block end in this buffer, after
+          // a refill of the buffer, which needs every warp's release of it
+          // (the last warp's after its sums).
+          constexpr int DN = C::EPV / C::ES;
+          Ff f[DN];
+#pragma unroll
+          for (int e = 0; e < C::EPV; ++e)
+            if (e / DN == el) f[e % DN] = ff_square(acc[e]);
+          int base = 0;
+          halve_rows<DN, C::LPR * C::ES>(f, lane, base);
+          constexpr int NF = halved_count(DN, C::LPR * C::ES);
+          constexpr int DUP = halved_dup_mask(DN, C::LPR * C::ES);
+          float2* red = dpair + (size_t)buf * C::NC * ST;
+          if ((lane & DUP) == 0) {
+#pragma unroll
+            for (int i = 0; i < NF; ++i) red[warp * ST + el * DN + base + i] = make_float2(f[i].h, f[i].l);
+          }
+          __syncwarp();
+          int done = 0;
+          if (lane == 0) {
+            __threadfence_block();
+            done = atomicAdd(&dcnt[buf], 1);
+            __threadfence_block();
+          }
+          __syncwarp();
+          done = __shfl_sync(0xffffffffu, done, 0);
+          if (done == C::NC - 1) {
+            __threadfence_block();
+            if (lane < ST) {
+              Ff t = {red[lane].x, red[lane].y};
+              for (int w = 1; w < C::NC; ++w) t = sum2(t, Ff{red[w * ST + lane].x, red[w * ST + lane].y});
+              const int e2 =
+                  2 * (ceil_log2_exp_p(__uint_as_float(__ldg(P.in_max + tile * ST + lane))) - P.mat_scale_exp);
+              P.dot[(size_t)(tile * ST + lane) * P.nblocks + b] = ldexp((double)t.h + (double)t.l, e2);
+            }
+            __syncwarp();
+            if (lane == 0) dcnt[buf] = 0;
+          }
+        }
+      } else if (P.dot) {
         // per-slice squared norm of the block's rows: lanes sharing `sub`
         // hold the same slices (reduce over rows by shuffles), then the 16
         // consumer warps combine through shared memory in a fixed order.
@@ -774,7 +857,7 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
   }
 }
 
-size_t pipe_smem_bytes(int cap, int64_t emax, int64_t desc_bytes, int pixb, int eb, int nb,
+size_t pipe_smem_bytes(int cap, int64_t emax, int64_t desc_bytes, int pixb, int xb, int eb, int nb,
                        uint32_t* xbytes, uint32_t* ebytes, uint32_t* dbytes) {
   const size_t x = ((size_t)(cap + 1) * pixb + 127) / 128 * 128;
   const size_t e = ((size_t)emax * eb + 127) / 128 * 128;
@@ -782,9 +865,12 @@ size_t pipe_smem_bytes(int cap, int64_t emax, int64_t desc_bytes, int pixb, int 
   if (xbytes) *xbytes = (uint32_t)x;
   if (ebytes) *ebytes = (uint32_t)e;
   if (dbytes) *dbytes = (uint32_t)d;
-  // stage buffers, descriptor slots, barriers, stage identities
+  // stage buffers, descriptor slots, barriers, stage identities; 16-byte
+  // rows of 16-bit slices: block-end partials (8 consumer warps x 8 slices
+  // of FP32 pairs per buffer) and their counters
+  const size_t red = (pixb == 16 && xb == 2) ? (size_t)nb * 8 * 8 * 8 + 16 * nb : 0;
   return nb * (x + e + 256 + 128) + kDescSlots * d + 8 * (2 * nb + kDescSlots + 2) +
-         16 * kDescSlots + 128;
+         16 * kDescSlots + red + 128;
 }
 
 // shared memory a pipeline CTA may use so that `minb` CTAs fit on an SM
@@ -847,7 +933,8 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   a.err = list[0].err;
   a.wait_ns = wait_limit_ns();
   static_assert(C::NB == pipe_nb(C::PIXB), "stage buffers");
-  const size_t smem = pipe_smem_bytes(cap, emax, dmax, C::PIXB, C::EB, C::NB, &a.xbytes, &a.ebytes,
+  static_assert(C::PIXB != 16 || !C::X16 || (C::NC == 8 && ST == 8), "block-end partial area");
+  const size_t smem = pipe_smem_bytes(cap, emax, dmax, C::PIXB, C::XB, C::EB, C::NB, &a.xbytes, &a.ebytes,
                                       &a.dbytes);
   static_assert(C::MINB == pipe_minb(C::PIXB), "CTAs per SM");
   const int per_sm = pipe_ctas_per_sm(smem, C::MINB);
@@ -930,7 +1017,8 @@ bool spmm_pipe_applies(const SpmmArgs& a) {
   if (a.L->nblocks == 0) return false;
   if (a.L->unit != kEntryRowBytes && (pixb != a.L->unit || !stages16(a.storage))) return false;
   const int64_t emax = a.L->unit == kEntryRowBytes ? a.L->emax_slots : 0;   // wide: not staged
-  return pipe_smem_bytes(a.L->cap, emax, a.L->desc_bytes, pixb, a.storage == XCT_F32 ? 8 : 4,
+  return pipe_smem_bytes(a.L->cap, emax, a.L->desc_bytes, pixb, stages16(a.storage) ? 2 : 4,
+                         a.storage == XCT_F32 ? 8 : 4,
                          pipe_nb(pixb), nullptr, nullptr, nullptr) <= pipe_cta_smem_max(kPipeMinCtas);
 }
 
@@ -952,7 +1040,8 @@ bool spmm_pipe_multi_applies(const SpmmArgs* list0, int count) {
     dmax = dmax > list[i].L->desc_bytes ? dmax : list[i].L->desc_bytes;
   }
   const int pixb = list[0].st * (stages16(list[0].storage) ? 2 : 4);
-  return pipe_smem_bytes(cap, emax, dmax, pixb, list[0].storage == XCT_F32 ? 8 : 4, pipe_nb(pixb),
+  return pipe_smem_bytes(cap, emax, dmax, pixb, stages16(list[0].storage) ? 2 : 4,
+                         list[0].storage == XCT_F32 ? 8 : 4, pipe_nb(pixb),
                          nullptr, nullptr, nullptr) <= pipe_cta_smem_max(kPipeMinCtas);
 }
 
