@@ -545,6 +545,7 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
 #pragma unroll
   for (int i = 0; i < C::SPL; ++i) acc[i] = 0.0f;
   uint32_t rphase = 0;   // phase of the block-end rendezvous barriers
+  int live = 8;   // wide stages: live slices of the block's tile (2, 4 or 8)
   for (uint32_t it = 0;; ++it) {
     const int buf = (int)(it % NB);
     if (!mbar_wait(&full[buf], (it / NB) & 1, a.wait_ns)) {
@@ -556,6 +557,14 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
     if (h.kstage == 0) {
 #pragma unroll
       for (int i = 0; i < C::SPL; ++i) acc[i] = 0.0f;
+      if constexpr (WIDE) {
+        // live slices of the block's tile: 2 when slices 2 .. 7 are all
+        // zero (one or two slices, the rest padding), 4 when slices 4 .. 7
+        // are, else 8; only their bytes of each staged row are read
+        const uint32_t* im = a.L[h.prod].in_max + (h.work / a.L[h.prod].nblocks) * ST;
+        const uint32_t hi4 = __ldg(im + 4) | __ldg(im + 5) | __ldg(im + 6) | __ldg(im + 7);
+        live = hi4 != 0u ? 8 : ((__ldg(im + 2) | __ldg(im + 3)) != 0u ? 4 : 2);
+      }
     }
     if (h.np > 0) {
       const uint4 sgv = *reinterpret_cast<const uint4*>(sbuf(buf) + quad * 16);
@@ -578,22 +587,41 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
             reinterpret_cast<const uint4*>(reinterpret_cast<const uint32_t*>(a.L[h.prod].ent) + off) +
             gq * 4 + el;
         const uint4 z = make_uint4(0, 0, 0, 0);
-        int k = el;
-        uint4 n0 = k < nch ? __ldg(gp) : z;
-        uint4 n1 = k + 4 < nch ? __ldg(gp + 16) : z;
-        const uint4* pn = gp + 32;
-        for (; k < nch; k += 4) {
-          const uint4 cur = n0;
-          n0 = n1;
-          n1 = k + 8 < nch ? __ldg(pn) : z;
-          pn += 16;
-          const uint32_t e4[4] = {cur.x, cur.y, cur.z, cur.w};
-          uint4 xv[4];
+        // (with 2 or 4 live slices, 4 or 8 bytes of the row and 2 or 4 FMAs
+        // per entry: the other slices' accumulators stay zero)
+        auto rows = [&](auto live) {
+          constexpr int LV = decltype(live)::value;
+          int k = el;
+          uint4 n0 = k < nch ? __ldg(gp) : z;
+          uint4 n1 = k + 4 < nch ? __ldg(gp + 16) : z;
+          const uint4* pn = gp + 32;
+          for (; k < nch; k += 4) {
+            const uint4 cur = n0;
+            n0 = n1;
+            n1 = k + 8 < nch ? __ldg(pn) : z;
+            pn += 16;
+            const uint32_t e4[4] = {cur.x, cur.y, cur.z, cur.w};
+            uint4 xv[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) xv[q] = *reinterpret_cast<const uint4*>(xs + (e4[q] >> 16));
+            for (int q = 0; q < 4; ++q) {
+              if constexpr (LV == 2) {
+                xv[q] = make_uint4(*reinterpret_cast<const uint32_t*>(xs + (e4[q] >> 16)), 0u, 0u, 0u);
+              } else if constexpr (LV == 4) {
+                const uint2 v = *reinterpret_cast<const uint2*>(xs + (e4[q] >> 16));
+                xv[q] = make_uint4(v.x, v.y, 0u, 0u);
+              } else
+                xv[q] = *reinterpret_cast<const uint4*>(xs + (e4[q] >> 16));
+            }
 #pragma unroll
-          for (int q = 0; q < 4; ++q) PFma<TX, TW, C::EPV>::run(acc, xv[q], e4[q] & 0xffffu);
-        }
+            for (int q = 0; q < 4; ++q) PFma<TX, TW, LV>::run(acc, xv[q], e4[q] & 0xffffu);
+          }
+        };
+        if (live == 2)
+          rows(std::integral_constant<int, 2>{});
+        else if (live == 4)
+          rows(std::integral_constant<int, 4>{});
+        else
+          rows(std::integral_constant<int, C::EPV>{});
       } else if constexpr (C::ES > 1) {
         // EPL entries of each chunk per lane; four entries in flight per step
         constexpr int EPL = 4 / C::ES;

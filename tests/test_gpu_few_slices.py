@@ -55,12 +55,13 @@ def test_wide_products_vs_oracle_model(xct, kind, n, m, nd, S, off):
                oracle.project(absm, np.abs(v)))
 
 
-def test_wide_cgls_stable_phase_vs_oracle_model(xct):
-    """Four noisy slices, k = 1, 3, 5: within 1e-4 of the oracle's model of
-    the binary16 solve (the bar of the mixed CGLS test)."""
+@pytest.mark.parametrize("S", [2, 3, 5])
+def test_wide_cgls_stable_phase_vs_oracle_model(xct, S):
+    """Two, three or five noisy slices (the 2-, 4- and 8-slice paths of a
+    wide tile), k = 1, 3, 5: within 1e-4 of the oracle's model of the
+    binary16 solve (the bar of the mixed CGLS test)."""
     import _mixed_envelope as me
-    n, m, nd, S, cs, sino, a, at = me.noisy_batch()
-    S = 4
+    n, m, nd, _, cs, sino, a, at = me.noisy_batch()
     b = sino[:S]
     bt = torch.tensor(b, dtype=torch.float32, device="cuda")
     b32 = me._to_f32(b.reshape(S, -1))
