@@ -688,7 +688,8 @@ def run_ours(args):
         "vs_fp64": vs64,
         "accuracy_vs_fp64": accuracy,
         "hbm_regime": {"storage": "f16", "note": "few slices: the packed matrix stream (nnz x 4 B) "
-                       "sets the roof; slice counts below 8 run as an 8-slice tile; by_slices: the "
+                       "sets the roof; slice counts below 8 run as an 8-slice tile (on wide stages only its 2 or 4 "
+                       "live slices are read and multiplied when the rest are padding); by_slices: the "
                        "plan's own layouts, by_slices_wide: a plan built with XCT_PLAN_FEW_SLICES "
                        "(wide stages, entries streamed from device memory)", "by_slices": hbm_regime,
                        "by_slices_wide": hbm_regime_wide,
