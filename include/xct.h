@@ -95,8 +95,9 @@ typedef struct xct_plan_s* xct_plan_t;
                                  slice tile (about 3x the layout time) */
 #define XCT_PLAN_FEW_SLICES 4u  /* XCT_F16 / XCT_BF16 only: also build
                                    wide-stage layouts of A and A^T (stages of
-                                   up to 1016 staged rows, the packed entries
-                                   read straight from device memory) for
+                                   up to 1524 (A) / 1016 (A^T) staged rows,
+                                   the packed entries read straight from
+                                   device memory) for
                                    products of at most 8 slices, where the
                                    matrix stream from HBM is the lowest roof
                                    (Sec. III-B, roofline: input buffering of

@@ -1394,13 +1394,13 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
   }
   const int32_t cap_used = p.la.cap;
   // wide-stage layouts for products of few slices (16-byte staged rows):
-  // stages of up to kWideCap rows, gaps of up to kWideGap unreferenced rows
+  // stages of up to kWideCapA / kWideCapAT rows, gaps of up to kWideGap unreferenced rows
   // filled, offsets at 16 bytes per row; the entries stay in global memory
   if (p.flags & XCT_PLAN_FEW_SLICES) {
     for (int which = 0; which < 2; ++which) {
       Arena mem(s);
       Layout& out = which == 0 ? p.law : p.latw;
-      XCT_TRY(build_layout(which == 0 ? ma : mt, p.nnz, p.storage, kWideCap, out, mem, s, kWideGap,
+      XCT_TRY(build_layout(which == 0 ? ma : mt, p.nnz, p.storage, which == 0 ? kWideCapA : kWideCapAT, out, mem, s, kWideGap,
                            kWideRowBytes));
       mem.move_to(keep);
     }

@@ -1,6 +1,7 @@
 """Plans built with XCT_PLAN_FEW_SLICES: wide-stage layouts of A and A^T
-(up to 1016 staged 16-byte rows a stage, the packed entries read straight
-from device memory) serve products of at most 8 binary16 / bfloat16 slices.
+(up to 1524 / 1016 staged 16-byte rows a stage for A / A^T, the packed
+entries read straight from device memory) serve products of at most 8
+binary16 / bfloat16 slices.
 Their products are checked element by element against the oracle's model of
 the 16-bit semantics at the bars of the product tests, their CGLS over the
 stable phase against the oracle's model of the mixed solve, and a batch that
