@@ -961,7 +961,8 @@ def _measure_tv(reps, with_autograd=True):
     n, m, nd, S, steps = w["n"], w["m"], w["nd"], w["slices"], w["iters"]
     lam, eps, lr = 1e-3, 1e-3, 1e-2
     stream = torch.cuda.current_stream()
-    plan = xct.Plan(n, m, nd, "bf16", cos_sin=w["cos_sin"])
+    # 16-slice tiles: the plan orders each 4-row group's entries for them
+    plan = xct.Plan(n, m, nd, "bf16", cos_sin=w["cos_sin"], narrow_tiles=True)
     nnz = plan.stats()["nnz"]
     y = torch.tensor(w["sino"], dtype=torch.float32, device="cuda")
     x = torch.empty((S, n, n), device="cuda")
@@ -994,7 +995,7 @@ def _measure_tv(reps, with_autograd=True):
     plan.close()
     return {"metric": "Adam steps/s and product GFLOP/s (2 products of 2*nnz*S flops per step)",
             "n": n, "angles": m, "bins": nd, "slices": S, "steps": steps, "storage": "bf16",
-            "nnz": nnz, **res, "cost_first": float(lh[0]), "cost_last": float(lh[-1])}
+            "plan_flags": "XCT_PLAN_NARROW_TILES", "nnz": nnz, **res, "cost_first": float(lh[0]), "cost_last": float(lh[-1])}
 
 
 def run_tv(args):
@@ -1029,7 +1030,9 @@ def _measure_large(steps, warmup):
     res = {}
     xs = {}
     for kind in ("f16", "f32"):
-        plan = xct.Plan(n, m, nd, kind, cos_sin=inputs.angle_table(m))
+        # 32-slice tiles: the binary16 plan orders each 4-row group's entries
+        # for them (XCT_PLAN_NARROW_TILES needs a 16-bit matrix)
+        plan = xct.Plan(n, m, nd, kind, cos_sin=inputs.angle_table(m), narrow_tiles=(kind == "f16"))
         st = plan.stats()
         x = torch.empty((S, n, n), device="cuda")
         for _ in range(warmup):
@@ -1048,6 +1051,7 @@ def _measure_large(steps, warmup):
         ms = e0.elapsed_time(e1) / steps
         flops = (2 * K + 1) * 2.0 * st["nnz"] * S
         res[kind] = {"ms_per_solve": ms, "gflops": flops / (ms * 1e-3) / 1e9,
+                     "plan_flags": "XCT_PLAN_NARROW_TILES" if kind == "f16" else "",
                      "project_ms": tp / steps, "backproject_ms": tb / steps,
                      "plan_ms": st["plan_ms"], "bytes_a": st["bytes_a"], "bytes_at": st["bytes_at"]}
         xs[kind] = x

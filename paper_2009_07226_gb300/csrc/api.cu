@@ -611,8 +611,12 @@ xct_status xct_plan(const xct_geometry* g, xct_dtype storage, uint32_t flags, vo
     set_error("storage %d is not XCT_F32, XCT_F16, XCT_BF16, XCT_F16A or XCT_BF16A", (int)storage);
     return XCT_ERR_INVALID;
   }
-  if (flags & ~(XCT_PLAN_KEEP_F64 | XCT_PLAN_AUTOTUNE | XCT_PLAN_FEW_SLICES)) {
+  if (flags & ~(XCT_PLAN_KEEP_F64 | XCT_PLAN_AUTOTUNE | XCT_PLAN_FEW_SLICES | XCT_PLAN_NARROW_TILES)) {
     set_error("unknown plan flags 0x%x", flags);
+    return XCT_ERR_INVALID;
+  }
+  if ((flags & XCT_PLAN_NARROW_TILES) && !matrix16(storage)) {
+    set_error("XCT_PLAN_NARROW_TILES needs a 16-bit matrix storage (XCT_F16, XCT_BF16, XCT_F16A, XCT_BF16A)");
     return XCT_ERR_INVALID;
   }
   if ((flags & XCT_PLAN_FEW_SLICES) && !stages16(storage)) {

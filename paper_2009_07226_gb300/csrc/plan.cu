@@ -947,9 +947,62 @@ __global__ void wide_order_kernel(const uint32_t* src, uint32_t* ent, const Seg*
   }
 }
 
+// Entry order of a 280-row layout (128-byte staged-row offsets) for the
+// narrower slice tiles that read it (plans built with XCT_PLAN_NARROW_TILES).  With 32-byte rows (16 slices) the
+// lanes of a quad's 4 rows read their k-th entries together (one phase of a
+// 16-byte load), staged row j lying in the 8-bank group j mod 4; with
+// 64-byte rows (32 slices) rows 2h and 2h + 1 share a phase, row j in bank
+// half j mod 2.  So at every entry index the plan gives the quad's rows
+// distinct residues mod 4 where the counts allow, rows 2h and 2h + 1 of
+// different parity where it can: for each row, the free residue with the
+// most entries left (for the second row of a pair, one of the other parity
+// first).  The order of a row's entries is free (its sum changes only by
+// FP32 rounding); padding stays at the end of each row.  `src` is a copy of
+// the entries in CSR order; one thread per (stage, quad).
+__global__ void quad_order_kernel(const uint32_t* src, uint32_t* ent, const Seg* seg, int64_t nquads) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nquads;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const Seg sg = seg[t];
+    int cnt[4], left[4][4], scan[4][4];
+    int kmax = 0;
+    for (int g = 0; g < 4; ++g) {
+      cnt[g] = sg.cnt[g];
+      kmax = kmax > cnt[g] ? kmax : cnt[g];
+      for (int b = 0; b < 4; ++b) left[g][b] = 0, scan[g][b] = 0;
+    }
+    auto slot = [&](int g, int k) { return sg.off + (k >> 2) * 16 + g * 4 + (k & 3); };
+    auto group = [&](uint32_t e) { return (int)((e >> 23) & 3u); };   // (offset / 128) mod 4
+    for (int g = 0; g < 4; ++g)
+      for (int k = 0; k < cnt[g]; ++k) ++left[g][group(src[slot(g, k)])];
+    for (int k = 0; k < kmax; ++k) {
+      uint32_t used = 0;
+      int pick[4] = {-1, -1, -1, -1};
+      for (int g = 0; g < 4; ++g) {
+        if (k >= cnt[g]) continue;
+        const int partner = (g & 1) ? pick[g - 1] : -1;
+        int best = -1;
+        for (int pass = 0; pass < 3 && best < 0; ++pass)
+          for (int b = 0; b < 4; ++b) {
+            if (left[g][b] == 0) continue;
+            if (pass < 2 && ((used >> b) & 1u)) continue;
+            if (pass == 0 && partner >= 0 && (b & 1) == (partner & 1)) continue;
+            if (best < 0 || left[g][b] > left[g][best]) best = b;
+          }
+        int j = scan[g][best];   // an entry of group `best` lies at or after j
+        while (j < cnt[g] - 1 && group(src[slot(g, j)]) != best) ++j;
+        ent[slot(g, k)] = src[slot(g, j)];
+        scan[g][best] = j + 1;
+        --left[g][best];
+        used |= 1u << best;
+        pick[g] = best;
+      }
+    }
+  }
+}
+
 xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_t cap, Layout& L,
                         Arena& keep, cudaStream_t s, int gap = -1,
-                        int32_t unit = kEntryRowBytes) {
+                        int32_t unit = kEntryRowBytes, bool quad_order = false) {
   if (gap < 0) gap = gap_fill_for(storage);
   L.nrows = m.nrows;
   L.ncols = m.ncols;
@@ -1098,6 +1151,14 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
     const int64_t nhalf = L.nstages * kQuads * 2;
     wide_order_kernel<<<grid_for(nhalf, 128), 128, 0, s>>>(src, static_cast<uint32_t*>(L.ent), L.seg,
                                                            nhalf, ((uint32_t)cap * unit) << 16);
+    count_launch();
+  }
+  if (quad_order && unit == kEntryRowBytes && L.ebytes == 4 && L.nslots > 0) {
+    uint32_t* src;
+    XCT_TRY(tmp.get(&src, L.nslots));
+    XCT_TRY_CUDA(cudaMemcpyAsync(src, L.ent, sizeof(uint32_t) * L.nslots, cudaMemcpyDeviceToDevice, s));
+    const int64_t nq = L.nstages * kQuads;
+    quad_order_kernel<<<grid_for(nq, 128), 128, 0, s>>>(src, static_cast<uint32_t*>(L.ent), L.seg, nq);
     count_launch();
   }
   // stage descriptors: run lists padded to an even count of at least 2
@@ -1357,7 +1418,8 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
     for (int attempt = 0;; ++attempt) {
       Arena lm(s);
       Layout t;
-      XCT_TRY(build_layout(m, p.nnz, p.storage, cap, t, lm, s));
+      XCT_TRY(build_layout(m, p.nnz, p.storage, cap, t, lm, s, -1, kEntryRowBytes,
+                           (p.flags & XCT_PLAN_NARROW_TILES) != 0));
       if (kPipeBufs * pipe_buffer_bytes(t, 128) <= kPipeSmemLimit || attempt == 3 || cap <= 64) {
         L = t;
         lm.move_to(mem);

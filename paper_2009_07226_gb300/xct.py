@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libxct.so")
 XCT_OK, XCT_ERR_INVALID, XCT_ERR_OOM, XCT_ERR_CUDA = 0, 1, 2, 3
 XCT_ERR_TIMEOUT, XCT_ERR_BREAKDOWN, XCT_ERR_UNSUPPORTED = 4, 5, 6
 XCT_F32, XCT_F16, XCT_BF16, XCT_F16A, XCT_BF16A = 0, 1, 2, 3, 4
-XCT_PLAN_KEEP_F64, XCT_PLAN_AUTOTUNE, XCT_PLAN_FEW_SLICES = 1, 2, 4
+XCT_PLAN_KEEP_F64, XCT_PLAN_AUTOTUNE, XCT_PLAN_FEW_SLICES, XCT_PLAN_NARROW_TILES = 1, 2, 4, 8
 XCT_CGLS_X0, XCT_CGLS_NO_GRAPH, XCT_CGLS_TIMING = 1, 2, 4
 XCT_CGLS_SAVE, XCT_CGLS_RESUME = 32, 64
 XCT_EXPORT_A_F64, XCT_EXPORT_AT_F64, XCT_EXPORT_A_STORED, XCT_EXPORT_AT_STORED = 0, 1, 2, 3
@@ -409,14 +409,15 @@ class Plan:
     def __init__(self, n: int, n_angles: int, n_det: int | None = None, storage: str = "f32",
                  cos_sin=None, det_spacing: float = 1.0, det_offset: float = 0.0,
                  min_seg: float = 1e-9, hilbert_tile: int = 0, keep_f64: bool = False,
-                 autotune: bool = False, few_slices: bool = False, stream=None):
+                 autotune: bool = False, few_slices: bool = False, narrow_tiles: bool = False,
+                 stream=None):
         self.n, self.m = n, n_angles
         self.nd = n if n_det is None else n_det
         self.storage = storage
         self.geometry = make_geometry(n, n_angles, self.nd, cos_sin, det_spacing, det_offset,
                                       min_seg, hilbert_tile)
         flags = ((XCT_PLAN_KEEP_F64 if keep_f64 else 0) | (XCT_PLAN_AUTOTUNE if autotune else 0)
-                 | (XCT_PLAN_FEW_SLICES if few_slices else 0))
+                 | (XCT_PLAN_FEW_SLICES if few_slices else 0) | (XCT_PLAN_NARROW_TILES if narrow_tiles else 0))
         self.handle = xct_plan(self.geometry, storage, flags, stream)
 
     def close(self):
