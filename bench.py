@@ -482,8 +482,12 @@ def run_ours(args):
     y = torch.tensor(w["sino"], dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     # the FP32 plan also keeps the FP64 matrices for the double-precision yardstick
-    plans = {k: xct.Plan(n, m, nd, k, cos_sin=w["cos_sin"], keep_f64=(k == "f32"))
-             for k in ("f16", "f32", "f16a")}
+    # the binary16 plan also builds the paired layouts its 64-slice tiles run on
+    # (XCT_PLAN_PAIRED_ROWS); "f16u" is the same storage on the plain layouts,
+    # timed for comparison
+    plans = {k: xct.Plan(n, m, nd, "f16" if k == "f16u" else k, cos_sin=w["cos_sin"],
+                         keep_f64=(k == "f32"), paired_rows=(k == "f16"))
+             for k in ("f16", "f32", "f16a", "f16u")}
     nnz = plans["f16"].stats()["nnz"]
     flops_step = (2 * K + 1) * 2.0 * nnz * S
     xs = {k: torch.empty((S, n, n), dtype=torch.float32, device=dev) for k in plans}
@@ -523,7 +527,7 @@ def run_ours(args):
         return ms, tp / max(npj, 1), tb / max(nbp, 1), to / steps, launches
 
     timed.parts = {}
-    for kind in ("f16", "f32", "f16a"):
+    for kind in ("f16", "f32", "f16a", "f16u"):
         for _ in range(args.warmup):
             step(kind)
     torch.cuda.synchronize()
@@ -535,6 +539,7 @@ def run_ours(args):
     ms16, proj16, back16, other16, launches = timed("f16", args.steps)
     ms32, proj32, back32, other32, _ = timed("f32", args.steps)
     msa, proja, backa, othera, _ = timed("f16a", args.steps)
+    msu, proju, backu, otheru, _ = timed("f16u", args.steps)
     clocks = sampler.stop() if sampler else None
 
     # graph path (the default call) for reference, untimed by the roofline
@@ -648,12 +653,17 @@ def run_ours(args):
     # step alone on this GPU as a check of the first
     roof = _measure_roof(stream)
     fma_peak = fma_peak_derived
-    op16_peak = op16_peak_derived
+    # the paired layouts read one staged row per distinct column of a pair of
+    # rows (gathers_a_paired of them per tile) instead of one per entry: their
+    # operand roof is the plain one scaled by nnz / gathers
+    gathers = st16["gathers_a_paired"] or nnz
+    op16_peak_plain = op16_peak_derived
+    op16_peak = op16_peak_derived * nnz / gathers
     rows_a, cols_a = m * nd, n * n
     alg_bytes = nnz * 4 + (rows_a + 1) * 8 + S * cols_a * 2 + S * rows_a * 4
     alg_bytes_bp = nnz * 4 + (cols_a + 1) * 8 + S * rows_a * 2 + S * cols_a * 4
     hbm_roof = flops_launch / (alg_bytes / (peak_hbm * 1e9)) / 1e12
-    gather_bytes = nnz * S * 2
+    gather_bytes = gathers * S * 2
     smem_peak = 128.0 * nsm * clk / 1e9
     traffic = _profiled_traffic("spmm_pipe_f16_projection")
     value = flops_step / (ms16 * 1e-3) / 1e9
@@ -702,16 +712,27 @@ def run_ours(args):
         "roofline": {
             "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
-            "kernel": "spmm_pipe_kernel<__half,64> (projection, 2*nnz*S flops per launch)",
+            "kernel": "spmm_pipe_kernel<__half,__half,64,false,true> (projection on the paired layout, "
+                      "2*nnz*S flops per launch)",
             "peak_source": (f"derived at the median SM clock {sm_mhz:.0f} MHz, the least of three roofs: "
-                            f"the 16-bit operand roof {op16_peak:.1f} (each FMA reads 2 B of a staged row "
-                            f"from shared memory at 128 B/clk/SM: {nsm} SMs x 64 FMA/clk x 2 flop), which "
-                            f"the library's roof probe reaches to "
-                            f"{roof['gather16_mixed_fma']['tflops'] / op16_peak:.0%} with the product's "
-                            f"inner step alone ({roof['gather16_mixed_fma']['tflops']:.1f} measured); the "
-                            f"FP32 FMA roof {fma_peak:.1f} ({nsm} x 128 FMA/clk x 2 flop); the HBM roof "
+                            f"the 16-bit operand roof of the paired layout {op16_peak:.1f} (one 128-byte "
+                            f"staged row read from shared memory at 128 B/clk/SM per distinct column of a "
+                            f"pair of rows, {gathers / nnz:.3f} reads per entry; the plain layouts' "
+                            f"{op16_peak_plain:.1f} at one read per entry, {nsm} SMs x 64 FMA/clk x 2 flop, "
+                            f"which the library's roof probe reaches to "
+                            f"{roof['gather16_mixed_fma']['tflops'] / op16_peak_plain:.0%} with the plain "
+                            f"layouts' inner step alone, {roof['gather16_mixed_fma']['tflops']:.1f} measured); "
+                            f"the FP32 FMA roof {fma_peak:.1f} ({nsm} x 128 FMA/clk x 2 flop); the HBM roof "
                             f"{hbm_roof:.1f} (2*nnz*S flop over the algorithmic bytes at the measured "
                             f"{peak_hbm:.0f} GB/s)"),
+            "plain_layout": {"operand_roof": op16_peak_plain,
+                             "frac_of_plain_operand_roof": achieved / op16_peak_plain,
+                             "project_ms": proju, "backproject_ms": backu, "ms_per_step": msu,
+                             "value": flops_step / (msu * 1e-3) / 1e9,
+                             "achieved": flops_launch / (proju * 1e-3) / 1e12,
+                             "frac": flops_launch / (proju * 1e-3) / 1e12 / min(fma_peak, op16_peak_plain, hbm_roof),
+                             "note": "the same binary16 solve on a plan without XCT_PLAN_PAIRED_ROWS "
+                                     "(one staged-row read per entry)"},
             "roof_probe": {k: {**v, "fma_per_clk_per_sm": (v["ops_per_s"] / (nsm * clk)
                                                            if "tflops" in v else None)}
                            for k, v in roof.items()},
@@ -728,6 +749,8 @@ def run_ours(args):
         "e2e": {"value": flops_step / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
                 "h2d_bytes_per_step": int(S * m * nd * 4), "d2h_bytes_per_step": int(S * n * n * 4)},
         "plan_ms": {"f16": st16["plan_ms"], "f32": plans["f32"].stats()["plan_ms"]},
+        "plan_flags": {"f16": "XCT_PLAN_PAIRED_ROWS", "f32": "XCT_PLAN_KEEP_F64", "f16a": "",
+                       "f16u": ""},
     }
     c1 = None
     if world == 1 and not args.no_workloads:
@@ -773,7 +796,8 @@ def run_products(args):
     wl = inputs.WORKLOADS[WORKLOAD]
     n, m, nd = wl["n"], wl["m"], wl["nd"]
     S = args.slices or wl["slices"]
-    plan = xct.Plan(n, m, nd, args.storage, cos_sin=inputs.angle_table(m), few_slices=args.few_slices)
+    plan = xct.Plan(n, m, nd, args.storage, cos_sin=inputs.angle_table(m), few_slices=args.few_slices,
+                    paired_rows=args.paired_rows, narrow_tiles=args.narrow_tiles)
     g = torch.Generator(device="cuda").manual_seed(0)
     x = torch.rand((S, n, n), device="cuda", generator=g)
     y = torch.rand((S, m, nd), device="cuda", generator=g)
@@ -795,7 +819,8 @@ def run_products(args):
     tp, tb = e[0].elapsed_time(e[1]) / args.steps, e[1].elapsed_time(e[2]) / args.steps
     st = plan.stats()
     print(json.dumps({"mode": "products", "storage": args.storage, "nnz": nnz, "slices": S,
-                      "few_slices": args.few_slices,
+                      "few_slices": args.few_slices, "paired_rows": args.paired_rows,
+                      "narrow_tiles": args.narrow_tiles,
                       "stages_a": st["stages_a"], "stages_at": st["stages_at"],
                       "slots_a": st["slots_a"], "slots_at": st["slots_at"],
                       "bytes_a": st["bytes_a"], "bytes_at": st["bytes_at"],
@@ -1216,6 +1241,10 @@ def main():
                     help="--mode products: slices per product (default: the workload's 64)")
     ap.add_argument("--few-slices", action="store_true",
                     help="--mode products: build the plan with XCT_PLAN_FEW_SLICES (wide-stage layouts)")
+    ap.add_argument("--paired-rows", action="store_true",
+                    help="--mode products: build the plan with XCT_PLAN_PAIRED_ROWS (paired layouts, 64-slice tiles)")
+    ap.add_argument("--narrow-tiles", action="store_true",
+                    help="--mode products: build the plan with XCT_PLAN_NARROW_TILES")
     args = ap.parse_args()
     if args.mode == "products":
         run_products(args)

@@ -111,6 +111,20 @@ typedef struct xct_plan_s* xct_plan_t;
                                      / 2.7% faster products; 64-slice tiles
                                      0.7% slower, 8-slice tiles of a plan
                                      without XCT_PLAN_FEW_SLICES 3% slower) */
+#define XCT_PLAN_PAIRED_ROWS 16u  /* XCT_F16 / XCT_BF16 only: also build
+                                     paired layouts of A and A^T for 64-slice
+                                     tiles (128-byte staged rows): the two
+                                     rows of each pair (neighbouring angles
+                                     through one bin; neighbouring pixels)
+                                     share one gather of a staged row for
+                                     every column both cross (Sec. III-B
+                                     register reuse, taken across rows), so
+                                     a product reads about 0.7 (A) / 0.76
+                                     (A^T) of the staged rows it otherwise
+                                     would; products of other tile widths
+                                     use the plan's own layouts.  Adds about
+                                     1.2x the packed entries of A and A^T to
+                                     the plan (8 bytes a slot) */
 
 /*
  * xct_plan -- build the memoized operator (Sec. II-B memoization; Sec. III-A1
@@ -343,6 +357,13 @@ typedef struct {
   /* the parts of t_other_ms: 16-bit staging of the product inputs, vector
      updates (and layout conversions), FP64 scalar kernels */
   double t_stage_ms, t_vector_ms, t_scalar_ms;
+  /* 8-byte slots of the paired layouts of A and A^T (XCT_PLAN_PAIRED_ROWS;
+     0 without them), padding included */
+  int64_t slots_a_paired, slots_at_paired;
+  /* staged-row reads of one 64-slice tile on the paired layouts, padding
+     aside: the distinct columns of each pair of rows, summed over the stages
+     (the plain layouts read one staged row per entry, nnz) */
+  int64_t gathers_a_paired, gathers_at_paired;
 } xct_stats;
 
 xct_status xct_plan_stats(xct_plan_t plan, xct_stats* out);
@@ -353,6 +374,11 @@ xct_status xct_plan_stats(xct_plan_t plan, xct_stats* out);
 #define XCT_EXPORT_A_STORED 2   /* A decoded from the packed kernel layout:
                                    the stored value, de-normalised */
 #define XCT_EXPORT_AT_STORED 3  /* A^T decoded likewise */
+#define XCT_EXPORT_A_PAIRED 4   /* A decoded from its paired layout, needs
+                                   XCT_PLAN_PAIRED_ROWS (XCT_ERR_INVALID
+                                   otherwise, or when the paired layout did
+                                   not fit the product kernel's buffers) */
+#define XCT_EXPORT_AT_PAIRED 5  /* A^T decoded likewise */
 
 /*
  * xct_plan_export -- copy a matrix to host memory in canonical form: natural

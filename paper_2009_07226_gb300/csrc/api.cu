@@ -611,7 +611,8 @@ xct_status xct_plan(const xct_geometry* g, xct_dtype storage, uint32_t flags, vo
     set_error("storage %d is not XCT_F32, XCT_F16, XCT_BF16, XCT_F16A or XCT_BF16A", (int)storage);
     return XCT_ERR_INVALID;
   }
-  if (flags & ~(XCT_PLAN_KEEP_F64 | XCT_PLAN_AUTOTUNE | XCT_PLAN_FEW_SLICES | XCT_PLAN_NARROW_TILES)) {
+  if (flags & ~(XCT_PLAN_KEEP_F64 | XCT_PLAN_AUTOTUNE | XCT_PLAN_FEW_SLICES | XCT_PLAN_NARROW_TILES |
+                XCT_PLAN_PAIRED_ROWS)) {
     set_error("unknown plan flags 0x%x", flags);
     return XCT_ERR_INVALID;
   }
@@ -621,6 +622,10 @@ xct_status xct_plan(const xct_geometry* g, xct_dtype storage, uint32_t flags, vo
   }
   if ((flags & XCT_PLAN_FEW_SLICES) && !stages16(storage)) {
     set_error("XCT_PLAN_FEW_SLICES needs XCT_F16 or XCT_BF16 storage");
+    return XCT_ERR_INVALID;
+  }
+  if ((flags & XCT_PLAN_PAIRED_ROWS) && !stages16(storage)) {
+    set_error("XCT_PLAN_PAIRED_ROWS needs XCT_F16 or XCT_BF16 storage");
     return XCT_ERR_INVALID;
   }
   std::unique_ptr<xct_plan_s> p(new xct_plan_s());
@@ -965,7 +970,7 @@ xct_status xct_plan_stats(xct_plan_t plan, xct_stats* out) {
 xct_status xct_plan_export(xct_plan_t plan, int32_t what, int64_t* rowptr, int32_t* col,
                            double* val, int64_t* nnz) {
   XCT_TRY(check_plan(plan));
-  if (!nnz || what < 0 || what > 3 || (rowptr && (!col || !val))) {
+  if (!nnz || what < 0 || what > 5 || (rowptr && (!col || !val))) {
     set_error("bad export arguments");
     return XCT_ERR_INVALID;
   }

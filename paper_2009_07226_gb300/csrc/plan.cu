@@ -1182,6 +1182,224 @@ xct_status build_layout(const CsrView& m, int64_t nnz, xct_dtype storage, int32_
   return XCT_OK;
 }
 
+// Paired layout of a 280-row layout of 16-bit values (XCT_PLAN_PAIRED_ROWS;
+// the slot placement is described with kPairUA in xct_internal.cuh).  The
+// positions of a row's entries in a stage are distinct (a ray crosses a pixel
+// once), so the columns two rows share are the intersection of two position
+// bitmaps (at most kMaxStageCap + 1 positions).  One thread per (stage,
+// quad); `src` is the plain layout's entries (row g's k-th entry of the
+// segment at off + (k / 4) * 16 + g * 4 + k % 4, any order within the row).
+constexpr int kPairBmWords = (kMaxStageCap + 1 + 31) / 32;
+
+__device__ __forceinline__ int pair_pos(uint32_t e) { return (int)((e >> 16) / (uint32_t)kEntryRowBytes); }
+
+__device__ __forceinline__ int64_t pair_src_slot(const Seg& sg, int g, int k) {
+  return sg.off + (int64_t)(k >> 2) * 16 + g * 4 + (k & 3);
+}
+
+__device__ void pair_bitmaps(const uint32_t* src, const Seg& sg, int p, uint32_t* b0, uint32_t* b1) {
+  for (int i = 0; i < kPairBmWords; ++i) b0[i] = 0u, b1[i] = 0u;
+  for (int k = 0; k < sg.cnt[2 * p]; ++k) {
+    const int q = pair_pos(src[pair_src_slot(sg, 2 * p, k)]);
+    b0[q >> 5] |= 1u << (q & 31);
+  }
+  for (int k = 0; k < sg.cnt[2 * p + 1]; ++k) {
+    const int q = pair_pos(src[pair_src_slot(sg, 2 * p + 1, k)]);
+    b1[q >> 5] |= 1u << (q & 31);
+  }
+}
+
+__host__ __device__ inline int pair_groups(int chunks, int per) { return (chunks + per - 1) / per; }
+
+__global__ void pair_count_kernel(const uint32_t* src, const Seg* seg, int64_t nquads, Seg* pseg,
+                                  int64_t* slots, unsigned long long* gathers) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nquads;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const Seg sg = seg[t];
+    Seg ps;
+    ps.off = 0;
+    unsigned long long uni = 0;   // distinct columns of the pairs: staged-row reads
+    for (int p = 0; p < 2; ++p) {
+      uint32_t b0[kPairBmWords], b1[kPairBmWords];
+      pair_bitmaps(src, sg, p, b0, b1);
+      int ns = 0;
+      for (int i = 0; i < kPairBmWords; ++i) ns += __popc(b0[i] & b1[i]);
+      const int c0 = sg.cnt[2 * p], c1 = sg.cnt[2 * p + 1];
+      const int nx = (c0 > c1 ? c0 : c1) - ns;
+      uni += (unsigned long long)(c0 + c1 - ns);
+      ps.cnt[2 * p] = (uint16_t)((ns + 1) >> 1);
+      ps.cnt[2 * p + 1] = (uint16_t)((nx + 1) >> 1);
+    }
+    const int ga = pair_groups(ps.cnt[0] > ps.cnt[2] ? ps.cnt[0] : ps.cnt[2], kPairUA);
+    const int gb = pair_groups(ps.cnt[1] > ps.cnt[3] ? ps.cnt[1] : ps.cnt[3], kPairUB);
+    pseg[t] = ps;
+    slots[t] = (int64_t)ga * 4 * kPairUA + (int64_t)gb * 4 * kPairUB;
+    if (uni) atomicAdd(gathers, uni);
+  }
+}
+
+// `dst` starts as padding (both halves of every slot: the zero slot, value
+// 0); `bad` counts segments whose lists disagree with the counted sizes
+// (none for a traced matrix)
+__global__ void pair_fill_kernel(const uint32_t* src, const Seg* seg, const Seg* pseg, int64_t nquads,
+                                 uint32_t* dst, unsigned int* bad) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nquads;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const Seg sg = seg[t], ps = pseg[t];
+    const int ga = pair_groups(ps.cnt[0] > ps.cnt[2] ? ps.cnt[0] : ps.cnt[2], kPairUA);
+    const int64_t reg_a = ps.off, reg_b = ps.off + (int64_t)ga * 4 * kPairUA;
+    for (int p = 0; p < 2; ++p) {
+      uint32_t b0[kPairBmWords], b1[kPairBmWords];
+      pair_bitmaps(src, sg, p, b0, b1);
+      const int c0 = sg.cnt[2 * p], c1 = sg.cnt[2 * p + 1];
+      const int ns_cap = 2 * ps.cnt[2 * p], nx_cap = 2 * ps.cnt[2 * p + 1];
+      // slot of index i among a pair's shared (split) slots: chunk i / 2,
+      // lane i % 2
+      auto sa = [&](int i) {
+        const int c = i >> 1, e = i & 1;
+        return reg_a + (int64_t)(c / kPairUA) * 4 * kPairUA + (2 * p + e) * kPairUA + c % kPairUA;
+      };
+      auto sb = [&](int i) {
+        const int c = i >> 1, e = i & 1;
+        return reg_b + (int64_t)(c / kPairUB) * 4 * kPairUB + (2 * p + e) * kPairUB + c % kPairUB;
+      };
+      int ns = 0, n0 = 0, n1 = 0;
+      for (int k = 0; k < c0; ++k) {
+        const uint32_t e = src[pair_src_slot(sg, 2 * p, k)];
+        const int q = pair_pos(e);
+        if ((b1[q >> 5] >> (q & 31)) & 1u) {
+          uint32_t f = 0u;
+          for (int j = 0; j < c1; ++j) {
+            const uint32_t h = src[pair_src_slot(sg, 2 * p + 1, j)];
+            if ((h >> 16) == (e >> 16)) { f = h; break; }
+          }
+          if (ns < ns_cap) {
+            dst[2 * sa(ns)] = e;
+            dst[2 * sa(ns) + 1] = f;
+          } else {
+            atomicAdd(bad, 1u);
+          }
+          ++ns;
+        } else {
+          if (n0 < nx_cap) dst[2 * sb(n0)] = e;
+          else atomicAdd(bad, 1u);
+          ++n0;
+        }
+      }
+      for (int k = 0; k < c1; ++k) {
+        const uint32_t e = src[pair_src_slot(sg, 2 * p + 1, k)];
+        const int q = pair_pos(e);
+        if ((b0[q >> 5] >> (q & 31)) & 1u) continue;
+        if (n1 < nx_cap) dst[2 * sb(n1) + 1] = e;
+        else atomicAdd(bad, 1u);
+        ++n1;
+      }
+    }
+  }
+}
+
+__global__ void pair_pad_kernel(uint32_t* dst, int64_t n, uint32_t zero_entry) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = zero_entry;
+}
+
+// The paired layout P of a built 280-row layout L of 16-bit values: the
+// stages, footprints, run lists and stage capacity are L's (shared, not
+// copied); segments, slots and stage descriptors are P's own.
+xct_status build_paired_layout(const Layout& L, Layout& P, Arena& keep, cudaStream_t s) {
+  if (L.ebytes != 4 || L.unit != kEntryRowBytes || L.cap > kMaxStageCap) {
+    set_error("paired layout: needs a 280-row layout of 16-bit values");
+    return XCT_ERR_INVALID;
+  }
+  P = Layout{};
+  P.nrows = L.nrows;
+  P.ncols = L.ncols;
+  P.nblocks = L.nblocks;
+  P.cap = L.cap;
+  P.ebytes = 8;
+  P.nstages = L.nstages;
+  P.footprint = L.footprint;
+  P.blk_stage = L.blk_stage;
+  P.stage_pix = L.stage_pix;
+  P.stage_np = L.stage_np;
+  P.pix = L.pix;
+  P.stage_run = L.stage_run;
+  P.runs = L.runs;
+  P.nruns = L.nruns;
+  P.run_max = L.run_max;
+  P.unit = kEntryRowBytes;
+  P.pair = true;
+  const int64_t nq = L.nstages * kQuads;
+  Arena tmp(s), own(s);
+  int64_t *slots, *slot_off;
+  unsigned int* bad;
+  unsigned long long *emax, *gath;
+  XCT_TRY(own.get(&P.seg, nq > 0 ? nq : 1));
+  XCT_TRY(tmp.get(&gath, 1));
+  XCT_TRY_CUDA(cudaMemsetAsync(gath, 0, sizeof(unsigned long long), s));
+  XCT_TRY(tmp.get(&slots, nq > 0 ? nq : 1));
+  XCT_TRY(tmp.get(&slot_off, nq + 1));
+  XCT_TRY(tmp.get(&bad, 1));
+  XCT_TRY(tmp.get(&emax, 1));
+  XCT_TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned int), s));
+  XCT_TRY_CUDA(cudaMemsetAsync(emax, 0, sizeof(unsigned long long), s));
+  const uint32_t* src = static_cast<const uint32_t*>(L.ent);
+  if (nq > 0) {
+    pair_count_kernel<<<grid_for(nq, 128, 152 * 64), 128, 0, s>>>(src, L.seg, nq, P.seg, slots, gath);
+    count_launch();
+  }
+  XCT_TRY(exclusive_scan_i64(slots, slot_off, nq, s));
+  if (nq > 0) {
+    seg_off_kernel<<<grid_for(nq, 256), 256, 0, s>>>(P.seg, slot_off, nq);
+    count_launch();
+  }
+  XCT_TRY_CUDA(cudaMemcpyAsync(&P.nslots, slot_off + nq, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  XCT_TRY(own.get(&P.stage_ent, P.nstages + 1));
+  stage_ent_kernel<<<grid_for(P.nstages + 1, 256), 256, 0, s>>>(slot_off, P.nstages, P.stage_ent, emax);
+  count_launch();
+  unsigned long long emax_h = 0, gath_h = 0;
+  XCT_TRY_CUDA(cudaMemcpyAsync(&emax_h, emax, sizeof(emax_h), cudaMemcpyDeviceToHost, s));
+  XCT_TRY_CUDA(cudaMemcpyAsync(&gath_h, gath, sizeof(gath_h), cudaMemcpyDeviceToHost, s));
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  P.emax_slots = (int64_t)emax_h;
+  P.gathers = (int64_t)gath_h;
+  uint2* ent;
+  XCT_TRY(own.get(&ent, P.nslots > 0 ? P.nslots : 1));
+  P.ent = ent;
+  if (P.nslots > 0) {
+    pair_pad_kernel<<<grid_for(2 * P.nslots, 256, 152 * 32), 256, 0, s>>>(
+        reinterpret_cast<uint32_t*>(ent), 2 * P.nslots, ((uint32_t)L.cap * kEntryRowBytes) << 16);
+    count_launch();
+  }
+  if (nq > 0) {
+    pair_fill_kernel<<<grid_for(nq, 128, 152 * 64), 128, 0, s>>>(src, L.seg, P.seg, nq,
+                                                                reinterpret_cast<uint32_t*>(ent), bad);
+    count_launch();
+  }
+  {
+    const int64_t stride = L.run_max < 2 ? 2 : (L.run_max + 1) & ~(int64_t)1;
+    P.desc_bytes = stage_desc_bytes(stride);
+    XCT_TRY(own.get(&P.desc, (size_t)(P.nstages > 0 ? P.nstages : 1) * P.desc_bytes));
+    if (P.nstages > 0) {
+      desc_fill_kernel<<<grid_for(P.nstages, 128, 152 * 16), 128, 0, s>>>(
+          P.stage_ent, P.stage_np, P.stage_run, P.runs, P.seg, P.nstages, stride, P.desc_bytes, P.desc);
+      count_launch();
+    }
+  }
+  unsigned int bad_h = 0;
+  XCT_TRY_CUDA(cudaMemcpyAsync(&bad_h, bad, sizeof(bad_h), cudaMemcpyDeviceToHost, s));
+  XCT_TRY_CUDA(cudaGetLastError());
+  XCT_TRY_CUDA(cudaStreamSynchronize(s));
+  if (bad_h != 0) {
+    set_error("paired layout: %u entries outside their counted lists", bad_h);
+    return XCT_ERR_CUDA;
+  }
+  P.bytes = P.nslots * 8 + nq * (int64_t)sizeof(Seg) + (P.nstages + 1) * 8 + P.nstages * P.desc_bytes;
+  own.move_to(keep);
+  return XCT_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1469,6 +1687,32 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
     p.la.wide = &p.law;
     p.lat.wide = &p.latw;
   }
+  // paired layouts for 64-slice tiles of 16-bit slices, kept where their
+  // stage buffers fit the persistent product (else those tiles use the plain
+  // layouts)
+  if (p.flags & XCT_PLAN_PAIRED_ROWS) {
+    int dummy_work = 0, dummy_err = 0;
+    for (int which = 0; which < 2; ++which) {
+      Layout& base = which == 0 ? p.la : p.lat;
+      Layout& out = which == 0 ? p.lap : p.latp;
+      Arena mem(s);
+      XCT_TRY(build_paired_layout(base, out, mem, s));
+      SpmmArgs probe{};
+      probe.L = &out;
+      probe.st = kEntryRowBytes / 2;
+      probe.ntiles = 1;
+      probe.storage = p.storage;
+      probe.work = &dummy_work;   // only tested for null
+      probe.err = &dummy_err;
+      if (spmm_pipe_applies(probe)) {
+        mem.move_to(keep);
+        base.paired = &out;
+      } else {
+        mem.release();
+        out = Layout{};
+      }
+    }
+  }
 
   if (p.flags & XCT_PLAN_KEEP_F64) {
     p.a_rowptr = rowptr; p.a_col = col; p.a_val = val;
@@ -1495,6 +1739,10 @@ xct_status build_plan(Plan& p, cudaStream_t s) {
   st.slots_at = p.lat.nslots;
   st.bytes_a = p.la.bytes;
   st.bytes_at = p.lat.bytes;
+  st.slots_a_paired = p.la.paired ? p.la.paired->nslots : 0;
+  st.slots_at_paired = p.lat.paired ? p.lat.paired->nslots : 0;
+  st.gathers_a_paired = p.la.paired ? p.la.paired->gathers : 0;
+  st.gathers_at_paired = p.lat.paired ? p.lat.paired->gathers : 0;
   st.plan_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
   return XCT_OK;
 }
@@ -1531,11 +1779,74 @@ xct_status d2h(std::vector<T>& h, const T* d, int64_t n) {
   return XCT_OK;
 }
 
+double stored_value(const Plan& p, uint16_t h) {
+  if (half_values(p.storage)) {
+    __half_raw hr;
+    hr.x = h;
+    return (double)__half2float(__half(hr)) * ldexp(1.0, -p.mat_scale_exp);
+  }
+  const uint32_t f = (uint32_t)h << 16;
+  float ff;
+  memcpy(&ff, &f, 4);
+  return (double)ff * ldexp(1.0, -p.mat_scale_exp);
+}
+
+// The entries of a paired layout (placement described with kPairUA): every
+// half of a slot whose offset is not the zero slot's is an entry; a shared
+// slot gives one entry to each row of its pair at the same column.
+xct_status decode_paired(const Layout& L, const Plan& p, int64_t nrows, const std::vector<int32_t>& row_inv,
+                         const std::vector<int32_t>& col_inv, std::vector<Coo>& coo) {
+  std::vector<int64_t> bs, sp;
+  std::vector<int32_t> px;
+  std::vector<Seg> sg;
+  std::vector<unsigned long long> e8;
+  XCT_TRY(d2h(bs, L.blk_stage, (int64_t)L.nblocks + 1));
+  XCT_TRY(d2h(sp, L.stage_pix, L.nstages + 1));
+  XCT_TRY(d2h(px, L.pix, L.footprint));
+  XCT_TRY(d2h(sg, L.seg, L.nstages * kQuads));
+  XCT_TRY(d2h(e8, static_cast<const unsigned long long*>(L.ent), L.nslots));
+  const uint32_t zero = (uint32_t)L.cap * kEntryRowBytes;
+  for (int32_t b = 0; b < L.nblocks; ++b)
+    for (int64_t st = bs[b]; st < bs[b + 1]; ++st)
+      for (int q = 0; q < kQuads; ++q) {
+        const Seg& s = sg[st * kQuads + q];
+        const int ga = (std::max(s.cnt[0], s.cnt[2]) + kPairUA - 1) / kPairUA;
+        for (int pr = 0; pr < 2; ++pr)
+          for (int region = 0; region < 2; ++region) {
+            const int per = region == 0 ? kPairUA : kPairUB;
+            const int64_t r0 = s.off + (region == 0 ? 0 : (int64_t)ga * 4 * kPairUA);
+            for (int c = 0; c < s.cnt[2 * pr + region]; ++c)
+              for (int e = 0; e < 2; ++e) {
+                const int64_t slot = r0 + (int64_t)(c / per) * 4 * per + (2 * pr + e) * per + c % per;
+                if (slot < 0 || slot >= L.nslots) {
+                  set_error("paired layout: slot outside the entries (block %d stage %lld)", b, (long long)st);
+                  return XCT_ERR_CUDA;
+                }
+                const uint32_t half[2] = {(uint32_t)(e8[slot] & 0xffffffffu), (uint32_t)(e8[slot] >> 32)};
+                for (int h = 0; h < 2; ++h) {
+                  uint32_t off = half[h] >> 16;
+                  if (region == 0) off = half[0] >> 16;   // a shared slot's column is its first half's
+                  if (off == zero) continue;
+                  const uint32_t idx = off / (uint32_t)kEntryRowBytes;
+                  const int64_t row = (int64_t)b * kRowsPerBlock + q * 4 + 2 * pr + h;
+                  if (off % (uint32_t)kEntryRowBytes || idx >= (uint32_t)(sp[st + 1] - sp[st]) || row >= nrows) {
+                    set_error("paired layout holds an out-of-range entry (block %d stage %lld)", b, (long long)st);
+                    return XCT_ERR_CUDA;
+                  }
+                  coo.push_back({row_inv[row], col_inv[px[sp[st] + idx]],
+                                 stored_value(p, (uint16_t)(half[h] & 0xffffu))});
+                }
+              }
+          }
+      }
+  return XCT_OK;
+}
+
 }  // namespace
 
 xct_status export_matrix(Plan& p, int what, int64_t* rowptr, int32_t* col, double* val,
                          int64_t* nnz) {
-  const bool tr = (what == XCT_EXPORT_AT_F64 || what == XCT_EXPORT_AT_STORED);
+  const bool tr = (what == XCT_EXPORT_AT_F64 || what == XCT_EXPORT_AT_STORED || what == XCT_EXPORT_AT_PAIRED);
   const int64_t nrows = tr ? p.npix : p.nray;
   std::vector<int32_t> row_inv, col_inv;  // ordered id -> natural id
   XCT_TRY(d2h(row_inv, tr ? p.pix_inv : p.ray_inv, nrows));
@@ -1555,6 +1866,13 @@ xct_status export_matrix(Plan& p, int what, int64_t* rowptr, int32_t* col, doubl
     coo.reserve((size_t)p.nnz);
     for (int64_t r = 0; r < nrows; ++r)
       for (int64_t e = rp[r]; e < rp[r + 1]; ++e) coo.push_back({row_inv[r], col_inv[cc[e]], vv[e]});
+  } else if (what == XCT_EXPORT_A_PAIRED || what == XCT_EXPORT_AT_PAIRED) {
+    const Layout* LP = (tr ? p.lat : p.la).paired;
+    if (!LP) {
+      set_error("paired export needs a plan built with XCT_PLAN_PAIRED_ROWS whose paired layouts fit");
+      return XCT_ERR_INVALID;
+    }
+    XCT_TRY(decode_paired(*LP, p, nrows, row_inv, col_inv, coo));
   } else {
     const Layout& L = tr ? p.lat : p.la;
     std::vector<int64_t> bs, sp;

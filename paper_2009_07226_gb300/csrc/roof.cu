@@ -29,11 +29,11 @@ __device__ float g_roof_sink;            // keeps the probe's results live
 __device__ __forceinline__ void mixed8(float* acc, const uint4& v, unsigned short w) {
   const uint32_t* x = reinterpret_cast<const uint32_t*>(&v);
 #pragma unroll
-  for (int e = 0; e < 4; ++e)
-    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
-        "fma.rn.f32.f16 %0, lo, %3, %0;\n\tfma.rn.f32.f16 %1, hi, %3, %1;\n\t}"
-        : "+f"(acc[2 * e]), "+f"(acc[2 * e + 1])
-        : "r"(x[e]), "h"(w));
+  for (int e = 0; e < 4; ++e) {
+    const unsigned short lo = (unsigned short)(x[e] & 0xffffu), hi = (unsigned short)(x[e] >> 16);
+    asm("fma.rn.f32.f16 %0, %1, %2, %0;" : "+f"(acc[2 * e]) : "h"(lo), "h"(w));
+    asm("fma.rn.f32.f16 %0, %1, %2, %0;" : "+f"(acc[2 * e + 1]) : "h"(hi), "h"(w));
+  }
 }
 
 template <int KIND>

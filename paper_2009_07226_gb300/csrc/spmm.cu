@@ -93,10 +93,9 @@ struct Fma<__half, EPV> {
       const uint32_t* x = reinterpret_cast<const uint32_t*>(&v);
 #pragma unroll
       for (int e = 0; e < EPV / 2; ++e) {
-        asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
-            "fma.rn.f32.f16 %0, lo, %3, %0;\n\tfma.rn.f32.f16 %1, hi, %3, %1;\n\t}"
-            : "+f"(acc[2 * e]), "+f"(acc[2 * e + 1])
-            : "r"(x[e]), "h"(w));
+        const unsigned short lo = (unsigned short)(x[e] & 0xffffu), hi = (unsigned short)(x[e] >> 16);
+        asm("fma.rn.f32.f16 %0, %1, %2, %0;" : "+f"(acc[2 * e]) : "h"(lo), "h"(w));
+        asm("fma.rn.f32.f16 %0, %1, %2, %0;" : "+f"(acc[2 * e + 1]) : "h"(hi), "h"(w));
       }
     }
   }
@@ -114,10 +113,9 @@ struct Fma<__nv_bfloat16, EPV> {
       const uint32_t* x = reinterpret_cast<const uint32_t*>(&v);
 #pragma unroll
       for (int e = 0; e < EPV / 2; ++e) {
-        asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
-            "fma.rn.f32.bf16 %0, lo, %3, %0;\n\tfma.rn.f32.bf16 %1, hi, %3, %1;\n\t}"
-            : "+f"(acc[2 * e]), "+f"(acc[2 * e + 1])
-            : "r"(x[e]), "h"(w));
+        const unsigned short lo = (unsigned short)(x[e] & 0xffffu), hi = (unsigned short)(x[e] >> 16);
+        asm("fma.rn.f32.bf16 %0, %1, %2, %0;" : "+f"(acc[2 * e]) : "h"(lo), "h"(w));
+        asm("fma.rn.f32.bf16 %0, %1, %2, %0;" : "+f"(acc[2 * e + 1]) : "h"(hi), "h"(w));
       }
     }
   }
@@ -479,8 +477,8 @@ xct_status spmm_run(const SpmmArgs& a0, cudaStream_t s) {
     return XCT_ERR_INVALID;
   }
   if (spmm_pipe_applies(a)) return spmm_pipe(a, s);
-  if (a.L->unit != kEntryRowBytes) {
-    set_error("wide-stage layout without a fitting persistent product");
+  if (a.L->unit != kEntryRowBytes || a.L->pair) {
+    set_error("wide-stage or paired layout without a fitting persistent product");
     return XCT_ERR_UNSUPPORTED;
   }
   if (matrix16(a.storage) && !stages16(a.storage)) {

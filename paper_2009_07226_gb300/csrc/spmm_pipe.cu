@@ -224,16 +224,20 @@ template <int EPV> struct PFma<float, __nv_bfloat16, EPV> {
     ffma2_row<EPV>(acc, __uint_as_float((wbits & 0xffffu) << 16), v);
   }
 };
+// 16-bit staged rows: one mixed-precision FMA per slice, each its own
+// instruction with 16-bit operands split from the 32-bit words in C (ptxas
+// then takes the halves in place: 5% fewer instructions and 2.5% faster
+// products than splitting both halves inside one asm block)
 template <int EPV> struct PFma<__half, __half, EPV> {
   static __device__ __forceinline__ void run(float* acc, const uint4& v, uint32_t wbits) {
     const unsigned short w = (unsigned short)wbits;
     const uint32_t* x = reinterpret_cast<const uint32_t*>(&v);
 #pragma unroll
-    for (int e = 0; e < EPV / 2; ++e)
-      asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
-          "fma.rn.f32.f16 %0, lo, %3, %0;\n\tfma.rn.f32.f16 %1, hi, %3, %1;\n\t}"
-          : "+f"(acc[2 * e]), "+f"(acc[2 * e + 1])
-          : "r"(x[e]), "h"(w));
+    for (int e = 0; e < EPV / 2; ++e) {
+      const unsigned short lo = (unsigned short)(x[e] & 0xffffu), hi = (unsigned short)(x[e] >> 16);
+      asm("fma.rn.f32.f16 %0, %1, %2, %0;" : "+f"(acc[2 * e]) : "h"(lo), "h"(w));
+      asm("fma.rn.f32.f16 %0, %1, %2, %0;" : "+f"(acc[2 * e + 1]) : "h"(hi), "h"(w));
+    }
   }
 };
 template <int EPV> struct PFma<__nv_bfloat16, __nv_bfloat16, EPV> {
@@ -241,11 +245,29 @@ template <int EPV> struct PFma<__nv_bfloat16, __nv_bfloat16, EPV> {
     const unsigned short w = (unsigned short)wbits;
     const uint32_t* x = reinterpret_cast<const uint32_t*>(&v);
 #pragma unroll
-    for (int e = 0; e < EPV / 2; ++e)
-      asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
-          "fma.rn.f32.bf16 %0, lo, %3, %0;\n\tfma.rn.f32.bf16 %1, hi, %3, %1;\n\t}"
-          : "+f"(acc[2 * e]), "+f"(acc[2 * e + 1])
-          : "r"(x[e]), "h"(w));
+    for (int e = 0; e < EPV / 2; ++e) {
+      const unsigned short lo = (unsigned short)(x[e] & 0xffffu), hi = (unsigned short)(x[e] >> 16);
+      asm("fma.rn.f32.bf16 %0, %1, %2, %0;" : "+f"(acc[2 * e]) : "h"(lo), "h"(w));
+      asm("fma.rn.f32.bf16 %0, %1, %2, %0;" : "+f"(acc[2 * e + 1]) : "h"(hi), "h"(w));
+    }
+  }
+};
+
+// A shared slot of a paired layout: one 16-byte vector of a staged row (8
+// slices) times the values of both rows of a pair; acc[0 .. 8) and
+// acc[8 .. 16) are the two rows' sums of the same 8 slices (two plain
+// vector FMAs: measured faster than one asm block feeding both rows).
+template <class TX> struct PFma2;
+template <> struct PFma2<__half> {
+  static __device__ __forceinline__ void run(float* acc, const uint4& v, uint32_t w0bits, uint32_t w1bits) {
+    PFma<__half, __half, 8>::run(acc, v, w0bits);
+    PFma<__half, __half, 8>::run(acc + 8, v, w1bits);
+  }
+};
+template <> struct PFma2<__nv_bfloat16> {
+  static __device__ __forceinline__ void run(float* acc, const uint4& v, uint32_t w0bits, uint32_t w1bits) {
+    PFma<__nv_bfloat16, __nv_bfloat16, 8>::run(acc, v, w0bits);
+    PFma<__nv_bfloat16, __nv_bfloat16, 8>::run(acc + 8, v, w1bits);
   }
 };
 
@@ -322,10 +344,13 @@ __host__ __device__ constexpr int halved_dup_mask(int n, int o) {
   return o >= 32 ? 0 : (n > 1 ? halved_dup_mask(n / 2, 2 * o) : (o | halved_dup_mask(1, 2 * o)));
 }
 
-template <class TX, class TW, int ST, bool WIDE>
+template <class TX, class TW, int ST, bool WIDE, bool PAIR>
 __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
     spmm_pipe_kernel(PipeArgs a) {
   using C = PCfg<TX, TW, ST>;
+  // paired layouts: 128-byte rows of 16-bit slices, 8-byte slots
+  static_assert(!PAIR || (C::X16 && C::W16 && C::PIXB == 128 && C::SWZ && !WIDE), "paired layout");
+  constexpr int EB = PAIR ? 8 : C::EB;
   extern __shared__ __align__(128) unsigned char smem[];
   const uint32_t bufbytes = a.xbytes + a.ebytes + 256 + 128;
   constexpr int NB = C::NB;
@@ -477,11 +502,11 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
       const unsigned char* dd = dslot(ds);
       const StageDescHead dh = *reinterpret_cast<const StageDescHead*>(dd);
       const int np = real ? (int)dh.np : 0;
-      const uint32_t eb = real ? dh.slots * (uint32_t)C::EB : 0u;
+      const uint32_t eb = real ? dh.slots * (uint32_t)EB : 0u;
       // a wide stage's entries, read by the consumers from global memory
       // about two stages from now, are brought into L2 before this warp
       // waits for the buffer (measured 3.5% faster than no prefetch)
-      if (WIDE && lane == 0 && eb) bulk_prefetch_l2(P.ent + (size_t)dh.e0 * C::EB, eb);
+      if (WIDE && lane == 0 && eb) bulk_prefetch_l2(P.ent + (size_t)dh.e0 * EB, eb);
       if (!mbar_wait(&empty[buf], (use & 1) ^ 1, a.wait_ns)) { ok = false; fail_it = it; break; }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       if (lane == 0) {
@@ -516,7 +541,7 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
                      &full[buf]);
           }
         }
-        if (!WIDE && lane == 0 && eb) bulk_g2s(ebuf(buf), P.ent + (size_t)dh.e0 * C::EB, eb, &full[buf]);
+        if (!WIDE && lane == 0 && eb) bulk_g2s(ebuf(buf), P.ent + (size_t)dh.e0 * EB, eb, &full[buf]);
       }
       // the single arrival of this phase; it also publishes the header
       __syncwarp();
@@ -575,7 +600,61 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
       const int cnt = (int)((cw >> ((gq & 1) * 16)) & 0xffffu);
       const int nch = (cnt + 3) >> 2;
       const unsigned char* xs = xbuf(buf) + sub * C::VB;
-      if constexpr (WIDE) {
+      if constexpr (PAIR) {
+        // paired layout (placement described with kPairUA): lane 16 p + 8 e
+        // + j holds slices 8 j .. 8 j + 7 of both rows of pair p and takes
+        // the pair's slots of lane index e; the 8 lanes of a quarter warp
+        // read one whole 128-byte staged row per slot
+        static_assert(kPairUA == 4 && kPairUB == 2, "slot loads below");
+        const int pp = lane >> 4, pe = (lane >> 3) & 1;
+        const uint32_t cwp = pp ? sgv.w : sgv.z;
+        const int nsc = (int)(cwp & 0xffffu), nxc = (int)(cwp >> 16);
+        const int s0c = (int)(sgv.z & 0xffffu), s1c = (int)(sgv.w & 0xffffu);
+        const int ga = ((s0c > s1c ? s0c : s1c) + kPairUA - 1) / kPairUA;
+        const uint2* eq = reinterpret_cast<const uint2*>(ebuf(buf) + (off - base) * EB);
+        const unsigned char* xp = xbuf(buf) + (lane & 7) * C::VB;
+        // shared slots: one staged-row vector for both rows
+        const uint2* ea = eq + (2 * pp + pe) * kPairUA;
+        int c = 0;
+        for (; c + kPairUA <= nsc; c += kPairUA) {
+          const uint4* e4 = reinterpret_cast<const uint4*>(ea + c * 4);
+          const uint4 u0 = e4[0], u1 = e4[1];
+          const uint32_t ex[4] = {u0.x, u0.z, u1.x, u1.z};
+          const uint32_t ey[4] = {u0.y, u0.w, u1.y, u1.w};
+          uint4 xv[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) xv[q] = *reinterpret_cast<const uint4*>(xp + (ex[q] >> 16));
+#pragma unroll
+          for (int q = 0; q < 4; ++q) PFma2<TX>::run(acc, xv[q], ex[q], ey[q]);
+        }
+        for (; c < nsc; ++c) {
+          const uint2 ev = ea[(c / kPairUA) * 4 * kPairUA + c % kPairUA];
+          PFma2<TX>::run(acc, *reinterpret_cast<const uint4*>(xp + (ev.x >> 16)), ev.x, ev.y);
+        }
+        // split slots: one column of each row
+        const uint2* ebp = eq + ga * 4 * kPairUA + (2 * pp + pe) * kPairUB;
+        for (c = 0; c + kPairUB <= nxc; c += kPairUB) {
+          const uint4 u = *reinterpret_cast<const uint4*>(ebp + c * 4);
+          const uint32_t ex[2] = {u.x, u.z}, ey[2] = {u.y, u.w};
+          uint4 x0[2], x1[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            x0[q] = *reinterpret_cast<const uint4*>(xp + (ex[q] >> 16));
+            x1[q] = *reinterpret_cast<const uint4*>(xp + (ey[q] >> 16));
+          }
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            PFma<TX, TW, C::EPV>::run(acc, x0[q], ex[q] & 0xffffu);
+            PFma<TX, TW, C::EPV>::run(acc + C::EPV, x1[q], ey[q] & 0xffffu);
+          }
+        }
+        for (; c < nxc; ++c) {
+          const uint2 ev = ebp[(c / kPairUB) * 4 * kPairUB + c % kPairUB];
+          PFma<TX, TW, C::EPV>::run(acc, *reinterpret_cast<const uint4*>(xp + (ev.x >> 16)), ev.x & 0xffffu);
+          PFma<TX, TW, C::EPV>::run(acc + C::EPV, *reinterpret_cast<const uint4*>(xp + (ev.y >> 16)),
+                                    ev.y & 0xffffu);
+        }
+      } else if constexpr (WIDE) {
         // wide stages: the row's chunks of 4 entries are read straight from
         // global memory (16 bytes per lane, two chunks in flight ahead of
         // the one in use); lane e of the row takes chunks e, e + 4, ...;
@@ -711,7 +790,19 @@ __global__ void __launch_bounds__(PCfg<TX, TW, ST>::NT, PCfg<TX, TW, ST>::MINB)
       const int tile = h.work / P.nblocks, b = h.work % P.nblocks;
       const int64_t row = (int64_t)b * kRowsPerBlock + rb;
       float* yt = P.y + (size_t)tile * P.nrows * ST;
-      if constexpr (C::SWZ) {
+      if constexpr (PAIR) {
+        // lanes 16 p + j and 16 p + 8 + j hold partial sums of the same
+        // slices of both rows of pair p: each adds its partner's (one FP32
+        // addition, the same value in both), then keeps in acc[0 .. 8) its
+        // own row, 2 p + e = lane / 8, whose slices 8 j .. 8 j + 7 are those
+        // the lane owns in the layout of the other 128-byte tiles below
+#pragma unroll
+        for (int i = 0; i < 2 * C::EPV; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 8);
+        if ((lane >> 3) & 1) {
+#pragma unroll
+          for (int i = 0; i < C::EPV; ++i) acc[i] = acc[C::EPV + i];
+        }
+      } else if constexpr (C::SWZ) {
         // the two lanes of a row hold the same slices in swapped halves:
         // each adds the partner's partial sums of both halves
 #pragma unroll
@@ -916,9 +1007,10 @@ constexpr int pipe_minb(int pixb) {
 }
 constexpr int pipe_nb(int pixb) { return pixb == 16 ? kPipeBufs16 : kPipeBufs; }
 
-template <class TX, class TW, int ST, bool WIDE>
+template <class TX, class TW, int ST, bool WIDE, bool PAIR = false>
 xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   using C = PCfg<TX, TW, ST>;
+  constexpr int EB = PAIR ? 8 : C::EB;
   // the block-end reduction reuses a buffer's staged-row area
   static_assert((size_t)C::NC * ST * sizeof(double) <= (size_t)65 * C::PIXB,
                 "reduction area must fit in the staged rows of the smallest stage buffer");
@@ -962,7 +1054,7 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   a.wait_ns = wait_limit_ns();
   static_assert(C::NB == pipe_nb(C::PIXB), "stage buffers");
   static_assert(C::PIXB != 16 || !C::X16 || (C::NC == 8 && ST == 8), "block-end partial area");
-  const size_t smem = pipe_smem_bytes(cap, emax, dmax, C::PIXB, C::XB, C::EB, C::NB, &a.xbytes, &a.ebytes,
+  const size_t smem = pipe_smem_bytes(cap, emax, dmax, C::PIXB, C::XB, EB, C::NB, &a.xbytes, &a.ebytes,
                                       &a.dbytes);
   static_assert(C::MINB == pipe_minb(C::PIXB), "CTAs per SM");
   const int per_sm = pipe_ctas_per_sm(smem, C::MINB);
@@ -976,7 +1068,7 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   int cur_dev = 0;
   XCT_TRY_CUDA(cudaGetDevice(&cur_dev));
   if (cur_dev < 0 || cur_dev >= kMaxDevices || configured_for[cur_dev].load() != (int)smem + 1) {
-    XCT_TRY_CUDA(cudaFuncSetAttribute(spmm_pipe_kernel<TX, TW, ST, WIDE>,
+    XCT_TRY_CUDA(cudaFuncSetAttribute(spmm_pipe_kernel<TX, TW, ST, WIDE, PAIR>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (cur_dev >= 0 && cur_dev < kMaxDevices) configured_for[cur_dev].store((int)smem + 1);
   }
@@ -985,7 +1077,7 @@ xct_status launch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   if (work == 0) return XCT_OK;
   const int grid = work < sms * per_sm ? work : sms * per_sm;
   XCT_TRY_CUDA(cudaMemsetAsync(a.work, 0, sizeof(int), st));
-  spmm_pipe_kernel<TX, TW, ST, WIDE><<<grid, C::NT, smem, st>>>(a);
+  spmm_pipe_kernel<TX, TW, ST, WIDE, PAIR><<<grid, C::NT, smem, st>>>(a);
   count_launch();
   XCT_TRY_CUDA(cudaGetLastError());
   return XCT_OK;
@@ -996,12 +1088,20 @@ xct_status dispatch_pipe(const SpmmArgs* list, int count, cudaStream_t st) {
   // the persistent form is built for staged rows of 16, 32, 64 or 128 bytes
   // (8, 16, 32 or 64 slices in 16 bits; 4, 8, 16 or 32 in FP32)
   for (int i = 1; i < count; ++i)
-    if (list[i].st != list[0].st) {
-      set_error("persistent product: products of one launch must share the tile width");
+    if (list[i].st != list[0].st || list[i].L->pair != list[0].L->pair) {
+      set_error("persistent product: products of one launch must share the tile width and layout kind");
       return XCT_ERR_INVALID;
     }
   switch (list[0].st * PBytes<TX>::v) {
-    case 128: return launch_pipe<TX, TW, 128 / PBytes<TX>::v, false>(list, count, st);
+    case 128:
+      if constexpr (PBytes<TX>::v == 2 && PBytes<TW>::v == 2) {
+        if (list[0].L->pair) return launch_pipe<TX, TW, 64, false, true>(list, count, st);
+      }
+      if (list[0].L->pair) {
+        set_error("persistent product: paired layouts need 16-bit slices and values");
+        return XCT_ERR_INVALID;
+      }
+      return launch_pipe<TX, TW, 128 / PBytes<TX>::v, false>(list, count, st);
     case 64: return launch_pipe<TX, TW, 64 / PBytes<TX>::v, false>(list, count, st);
     case 32: return launch_pipe<TX, TW, 32 / PBytes<TX>::v, false>(list, count, st);
     case 16:
@@ -1045,8 +1145,9 @@ bool spmm_pipe_applies(const SpmmArgs& a) {
   if (a.L->nblocks == 0) return false;
   if (a.L->unit != kEntryRowBytes && (pixb != a.L->unit || !stages16(a.storage))) return false;
   const int64_t emax = a.L->unit == kEntryRowBytes ? a.L->emax_slots : 0;   // wide: not staged
+  if (a.L->pair && (pixb != kEntryRowBytes || !stages16(a.storage))) return false;
   return pipe_smem_bytes(a.L->cap, emax, a.L->desc_bytes, pixb, stages16(a.storage) ? 2 : 4,
-                         a.storage == XCT_F32 ? 8 : 4,
+                         a.L->ebytes,
                          pipe_nb(pixb), nullptr, nullptr, nullptr) <= pipe_cta_smem_max(kPipeMinCtas);
 }
 
@@ -1060,7 +1161,8 @@ bool spmm_pipe_multi_applies(const SpmmArgs* list0, int count) {
   int64_t emax = 0, dmax = 0;
   for (int i = 0; i < count; ++i) {
     if (!spmm_pipe_applies(list[i]) || list[i].storage != list[0].storage ||
-        list[i].st != list[0].st || list[i].L->unit != list[0].L->unit)
+        list[i].st != list[0].st || list[i].L->unit != list[0].L->unit ||
+        list[i].L->pair != list[0].L->pair)
       return false;
     cap = cap > list[i].L->cap ? cap : list[i].L->cap;
     if (list[i].L->unit == kEntryRowBytes)
@@ -1069,7 +1171,7 @@ bool spmm_pipe_multi_applies(const SpmmArgs* list0, int count) {
   }
   const int pixb = list[0].st * (stages16(list[0].storage) ? 2 : 4);
   return pipe_smem_bytes(cap, emax, dmax, pixb, stages16(list[0].storage) ? 2 : 4,
-                         list[0].storage == XCT_F32 ? 8 : 4, pipe_nb(pixb),
+                         list[0].L->ebytes, pipe_nb(pixb),
                          nullptr, nullptr, nullptr) <= pipe_cta_smem_max(kPipeMinCtas);
 }
 

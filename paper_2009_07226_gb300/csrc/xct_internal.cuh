@@ -181,8 +181,32 @@ struct Layout {
   // the wide-stage layout of the same matrix for 16-byte staged rows (built
   // with XCT_PLAN_FEW_SLICES), used in place of this one for such tiles
   const Layout* wide = nullptr;
+  // the paired layout of the same matrix for 128-byte rows of 16-bit slices
+  // (built with XCT_PLAN_PAIRED_ROWS), used in place of this one for such
+  // tiles; `pair` marks a paired layout itself (its stages, staged rows and
+  // runs are those of the plain layout, its segments and 8-byte slots its own)
+  const Layout* paired = nullptr;
+  bool pair = false;
+  int64_t gathers = 0;         // paired: distinct columns of the pairs over all stages
+                               // (the staged-row reads of one tile, padding aside)
   int64_t bytes = 0;
 };
+
+// Paired layout (XCT_PLAN_PAIRED_ROWS).  Rows 2p and 2p + 1 of a quad form
+// pair p.  A pair's entries in a stage are split into shared slots, one per
+// column both rows cross ({offset << 16 | value of row 2p, offset << 16 |
+// value of row 2p + 1}), and split slots, one column of each row ({offset0 <<
+// 16 | value0, offset1 << 16 | value1}, the zero slot with value 0 where one
+// row has no entry left).  Two lanes of a pair take alternate slots (a chunk
+// is 2 slots).  A (stage, quad) segment holds the shared region, then the
+// split region; each region is a sequence of groups of kPairUA (shared) or
+// kPairUB (split) chunks, and in a group the kPair* slots of each (pair, lane)
+// are contiguous: slot u of lane e of pair p in group g of the shared region
+// lies at g * 4 * kPairUA + (2 p + e) * kPairUA + u.  Seg::cnt holds the
+// chunk counts {shared of pair 0, split of pair 0, shared of pair 1, split
+// of pair 1}; each region has as many groups as its longer pair needs.
+constexpr int kPairUA = 4;
+constexpr int kPairUB = 2;
 
 // Shared memory of one pipeline buffer (staged rows of `pixb` bytes, the
 // stage's packed entries, its segment headers and header) with its share of
@@ -232,6 +256,7 @@ struct Plan {
   int32_t* ray_inv = nullptr;
   Layout la, lat;
   Layout law, latw;              // wide-stage layouts (XCT_PLAN_FEW_SLICES)
+  Layout lap, latp;              // paired layouts (XCT_PLAN_PAIRED_ROWS)
   int32_t mat_scale_exp = 0;     // k: stored value = RN(l * 2^k)
   int* err = nullptr;            // device flag: a bounded wait in a kernel ran out
   // kept FP64 matrices (ordered ids), only with XCT_PLAN_KEEP_F64
@@ -285,9 +310,12 @@ struct SpmmArgs {
   int* err;                // device flag set to 1 if a bounded wait ran out
 };
 // The layout a product runs on: the matrix's wide-stage layout, where the
-// plan built one, for 16-byte staged rows of 16-bit slices; else its own.
+// plan built one, for 16-byte staged rows of 16-bit slices; its paired
+// layout, where the plan built one, for 128-byte staged rows of 16-bit
+// slices; else its own.
 inline SpmmArgs on_product_layout(SpmmArgs a) {
   if (a.L->wide && stages16(a.storage) && a.st * 2 == kWideRowBytes) a.L = a.L->wide;
+  else if (a.L->paired && stages16(a.storage) && a.st * 2 == kEntryRowBytes) a.L = a.L->paired;
   return a;
 }
 xct_status spmm(const SpmmArgs& a, cudaStream_t s);   // = spmm_stage + spmm_run

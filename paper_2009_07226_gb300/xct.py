@@ -21,9 +21,11 @@ XCT_OK, XCT_ERR_INVALID, XCT_ERR_OOM, XCT_ERR_CUDA = 0, 1, 2, 3
 XCT_ERR_TIMEOUT, XCT_ERR_BREAKDOWN, XCT_ERR_UNSUPPORTED = 4, 5, 6
 XCT_F32, XCT_F16, XCT_BF16, XCT_F16A, XCT_BF16A = 0, 1, 2, 3, 4
 XCT_PLAN_KEEP_F64, XCT_PLAN_AUTOTUNE, XCT_PLAN_FEW_SLICES, XCT_PLAN_NARROW_TILES = 1, 2, 4, 8
+XCT_PLAN_PAIRED_ROWS = 16
 XCT_CGLS_X0, XCT_CGLS_NO_GRAPH, XCT_CGLS_TIMING = 1, 2, 4
 XCT_CGLS_SAVE, XCT_CGLS_RESUME = 32, 64
 XCT_EXPORT_A_F64, XCT_EXPORT_AT_F64, XCT_EXPORT_A_STORED, XCT_EXPORT_AT_STORED = 0, 1, 2, 3
+XCT_EXPORT_A_PAIRED, XCT_EXPORT_AT_PAIRED = 4, 5
 
 STORAGE = {"f32": XCT_F32, "f16": XCT_F16, "bf16": XCT_BF16, "f16a": XCT_F16A,
            "bf16a": XCT_BF16A}
@@ -55,7 +57,9 @@ class xct_stats(ctypes.Structure):
                 ("t_backproject_ms", ctypes.c_double), ("t_other_ms", ctypes.c_double),
                 ("n_project", ctypes.c_int64), ("n_backproject", ctypes.c_int64),
                 ("t_stage_ms", ctypes.c_double), ("t_vector_ms", ctypes.c_double),
-                ("t_scalar_ms", ctypes.c_double)]
+                ("t_scalar_ms", ctypes.c_double), ("slots_a_paired", ctypes.c_int64),
+                ("slots_at_paired", ctypes.c_int64), ("gathers_a_paired", ctypes.c_int64),
+                ("gathers_at_paired", ctypes.c_int64)]
 
 
 class xct_job(ctypes.Structure):
@@ -306,7 +310,7 @@ def xct_plan_export(plan: int, what: int):
     nnz = ctypes.c_int64()
     _check(lib().xct_plan_export(plan, what, None, None, None, ctypes.byref(nnz)))
     st = xct_plan_stats(plan)
-    nrows = st["n_pix"] if what in (XCT_EXPORT_AT_F64, XCT_EXPORT_AT_STORED) else st["n_rays"]
+    nrows = st["n_pix"] if what in (XCT_EXPORT_AT_F64, XCT_EXPORT_AT_STORED, XCT_EXPORT_AT_PAIRED) else st["n_rays"]
     rowptr = np.zeros(nrows + 1, dtype=np.int64)
     col = np.zeros(max(nnz.value, 1), dtype=np.int32)
     val = np.zeros(max(nnz.value, 1), dtype=np.float64)
@@ -410,14 +414,15 @@ class Plan:
                  cos_sin=None, det_spacing: float = 1.0, det_offset: float = 0.0,
                  min_seg: float = 1e-9, hilbert_tile: int = 0, keep_f64: bool = False,
                  autotune: bool = False, few_slices: bool = False, narrow_tiles: bool = False,
-                 stream=None):
+                 paired_rows: bool = False, stream=None):
         self.n, self.m = n, n_angles
         self.nd = n if n_det is None else n_det
         self.storage = storage
         self.geometry = make_geometry(n, n_angles, self.nd, cos_sin, det_spacing, det_offset,
                                       min_seg, hilbert_tile)
         flags = ((XCT_PLAN_KEEP_F64 if keep_f64 else 0) | (XCT_PLAN_AUTOTUNE if autotune else 0)
-                 | (XCT_PLAN_FEW_SLICES if few_slices else 0) | (XCT_PLAN_NARROW_TILES if narrow_tiles else 0))
+                 | (XCT_PLAN_FEW_SLICES if few_slices else 0) | (XCT_PLAN_NARROW_TILES if narrow_tiles else 0)
+                 | (XCT_PLAN_PAIRED_ROWS if paired_rows else 0))
         self.handle = xct_plan(self.geometry, storage, flags, stream)
 
     def close(self):
