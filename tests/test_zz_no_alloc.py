@@ -38,11 +38,14 @@ class _CountingAllocator:
         torch.cuda.caching_allocator_delete(ptr)
 
 
-@pytest.mark.parametrize("kind,S", [("f32", 5), ("f32", 40), ("f16", 17), ("f16", 64), ("bf16", 33)])
-def test_matches_xct_project_on_consecutive_calls(xct, kind, S):
+@pytest.mark.parametrize("kind,S,paired", [("f32", 5, False), ("f32", 40, False), ("f16", 17, False),
+                                            ("f16", 64, False), ("bf16", 33, False), ("f16", 64, True)])
+def test_matches_xct_project_on_consecutive_calls(xct, kind, S, paired):
+    """Also on a plan with paired layouts, whose 64-slice tiles run the
+    paired kernel in both calls."""
     n, m, nd = 96, 72, 100
     gen = torch.Generator(device="cuda").manual_seed(S)
-    with xct.Plan(n, m, nd, kind, det_offset=0.25) as p:
+    with xct.Plan(n, m, nd, kind, det_offset=0.25, paired_rows=paired) as p:
         for call in range(2):
             # a different magnitude per call: stale maxima or staging data from
             # the previous call would change the result
