@@ -119,12 +119,14 @@ typedef struct xct_plan_s* xct_plan_t;
                                      share one gather of a staged row for
                                      every column both cross (Sec. III-B
                                      register reuse, taken across rows), so
-                                     a product reads about 0.7 (A) / 0.76
-                                     (A^T) of the staged rows it otherwise
-                                     would; products of other tile widths
-                                     use the plan's own layouts.  Adds about
-                                     1.2x the packed entries of A and A^T to
-                                     the plan (8 bytes a slot) */
+                                     a product reads 0.71 (A) / 0.75 (A^T)
+                                     of the staged rows it otherwise would
+                                     at 512^2 x 768 angles (0.86 / 0.75 at
+                                     1536^2 x 1024, where neighbouring
+                                     angles diverge more); products of other
+                                     tile widths use the plan's own layouts.
+                                     Adds about 1.2x the packed entries of A
+                                     and A^T to the plan (8 bytes a slot) */
 
 /*
  * xct_plan -- build the memoized operator (Sec. II-B memoization; Sec. III-A1
