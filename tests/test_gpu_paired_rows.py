@@ -172,3 +172,85 @@ def test_paired_stats(xct):
     assert st["slots_a_paired"] > 0 and st["slots_at_paired"] > 0
     assert sq["slots_a_paired"] == 0 and sq["gathers_a_paired"] == 0
     assert st["slots_a"] == sq["slots_a"] and st["stages_a"] == sq["stages_a"]
+
+
+@pytest.mark.parametrize("S", [1, 8, 16, 32, 64, 130])
+def test_all_layout_flags_together(xct, S):
+    """A plan with paired, wide-stage and narrow-tile layouts at once: every
+    slice tile runs on its own layout (8-slice tiles on the wide stages,
+    16/32 on the reordered 280-row layouts, 64 on the paired ones), each
+    product within the bars of the oracle's 16-bit model."""
+    n, m, nd = 64, 96, 64
+    g = oracle.Geometry(n=n, m=m, nd=nd, cos_sin=inputs.angle_table(m))
+    a = oracle.siddon_csr(g)
+    at = oracle.transpose(a)
+    rng = np.random.default_rng(100 + S)
+    x = rng.uniform(0, 1, size=(S, n * n))
+    y = rng.uniform(0, 1, size=(S, m * nd))
+    with xct.Plan(n, m, nd, "f16", cos_sin=g.table(), paired_rows=True, few_slices=True,
+                  narrow_tiles=True) as p:
+        yo = p.project(torch.tensor(x.reshape(S, n, n), dtype=torch.float32, device="cuda"))
+        xo = p.backproject(torch.tensor(y.reshape(S, m, nd), dtype=torch.float32, device="cuda"))
+        torch.cuda.synchronize()
+    x32 = x.astype(np.float32).astype(np.float64)
+    y32 = y.astype(np.float32).astype(np.float64)
+    for got, mat, v in ((yo, a, x32), (xo, at, y32)):
+        absm = oracle.CSR(mat.nrow, mat.ncol, mat.rowptr, mat.col, np.abs(mat.val))
+        _check(got.cpu().numpy().reshape(S, -1), oracle.mixed_project(mat, v, "f16"),
+               oracle.project(absm, np.abs(v)))
+
+
+def test_paired_bf16_cgls_stable_phase_vs_oracle_model(xct):
+    """bfloat16 storage on paired layouts, 40 noisy slices, k = 1, 3, 5:
+    within 5e-4 of the oracle's model of the bfloat16 solve (the bar of the
+    mixed CGLS test for bfloat16)."""
+    import _mixed_envelope as me
+    n, m, nd, S0, cs, sino, a, at = me.noisy_batch()
+    b = np.concatenate([sino * (1.0 + 0.25 * j) for j in range(5)])
+    S = b.shape[0]
+    bt = torch.tensor(b, dtype=torch.float32, device="cuda")
+    b32 = me._to_f32(b.reshape(S, -1))
+    with xct.Plan(n, m, nd, "bf16", cos_sin=cs, paired_rows=True) as p:
+        for k in (1, 3, 5):
+            xmod, _ = oracle.cgls(*me.mixed_ops(a, at, "bf16"), b32, k)
+            xg = p.cgls(bt, k).cpu().numpy().reshape(S, -1)
+            assert np.linalg.norm(xg - xmod) / np.linalg.norm(xmod) <= 5e-4, k
+
+
+def test_paired_host_pipeline_equals_device(xct):
+    """Host-vector products over three 64-slice tiles (150 slices, the last
+    tile ragged) on paired layouts: the pipelined form equals the device
+    form bit for bit."""
+    n, m, nd, S = 64, 96, 64, 150
+    gen = torch.Generator().manual_seed(7)
+    x = torch.rand((S, n, n), generator=gen)
+    y = torch.rand((S, m, nd), generator=gen)
+    with xct.Plan(n, m, nd, "f16", cos_sin=inputs.angle_table(m), paired_rows=True) as p:
+        yd = p.project(x.cuda()).cpu()
+        xd = p.backproject(y.cuda()).cpu()
+        xh, yh = x.pin_memory(), y.pin_memory()
+        yo = torch.empty((S, m, nd)).pin_memory()
+        xo = torch.empty((S, n, n)).pin_memory()
+        xct.xct_project(p.handle, xh, yo, S, None)
+        xct.xct_backproject(p.handle, yh, xo, S, None)
+        torch.cuda.synchronize()
+    assert torch.equal(yo, yd) and torch.equal(xo, xd)
+
+
+def test_paired_resume_is_exact(xct):
+    """Checkpoint / resume on paired layouts: 3 iterations, save, 2 more
+    from the state equal 5 iterations in one solve bit for bit."""
+    import _mixed_envelope as me
+    n, m, nd, S0, cs, sino, a, at = me.noisy_batch()
+    b = np.concatenate([sino, sino * 1.5, sino * 0.5, sino * 2.0, sino * 0.75])
+    S = b.shape[0]
+    bt = torch.tensor(b, dtype=torch.float32, device="cuda")
+    with xct.Plan(n, m, nd, "f16", cos_sin=cs, paired_rows=True) as p:
+        ref = p.cgls(bt, 5)
+        state = torch.zeros(xct.xct_cgls_state_bytes(p.handle, S), dtype=torch.uint8, device="cuda")
+        x3 = torch.empty((S, n, n), device="cuda")
+        xct.xct_cgls_state(p.handle, bt, x3, S, 3, xct.XCT_CGLS_SAVE, state)
+        got = torch.empty_like(x3)
+        xct.xct_cgls_state(p.handle, None, got, S, 2, xct.XCT_CGLS_RESUME, state)
+        torch.cuda.synchronize()
+    assert torch.equal(got, ref)
