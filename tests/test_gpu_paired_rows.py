@@ -254,3 +254,49 @@ def test_paired_resume_is_exact(xct):
         xct.xct_cgls_state(p.handle, None, got, S, 2, xct.XCT_CGLS_RESUME, state)
         torch.cuda.synchronize()
     assert torch.equal(got, ref)
+
+
+def test_paired_products_write_every_output_and_repeat(xct):
+    """Poisoned (NaN-filled) outputs are overwritten everywhere, on a ragged
+    geometry (rows past the last block, rays that miss the grid), and two
+    runs give identical bits (no atomics on the paired path)."""
+    n, m, nd, S = 37, 23, 41, 64
+    rng = np.random.default_rng(9)
+    x = torch.tensor(rng.uniform(0, 1, size=(S, n, n)), dtype=torch.float32, device="cuda")
+    y = torch.tensor(rng.uniform(0, 1, size=(S, m, nd)), dtype=torch.float32, device="cuda")
+    with xct.Plan(n, m, nd, "f16", cos_sin=inputs.angle_table(m), det_offset=-0.4, paired_rows=True) as p:
+        outs = []
+        for _ in range(2):
+            yo = torch.full((S, m, nd), float("nan"), device="cuda")
+            xo = torch.full((S, n, n), float("nan"), device="cuda")
+            p.project(x, out=yo)
+            p.backproject(y, out=xo)
+            torch.cuda.synchronize()
+            assert not torch.isnan(yo).any() and not torch.isnan(xo).any()
+            outs.append((yo, xo))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+
+
+def test_paired_layouts_follow_the_autotuned_capacity(xct):
+    """With XCT_PLAN_AUTOTUNE the stage capacity is chosen by timing; the
+    paired layouts are built from the chosen layouts and their products
+    still meet the bars of the oracle's 16-bit model."""
+    n, m, nd, S = 96, 144, 100, 64
+    g = oracle.Geometry(n=n, m=m, nd=nd, cos_sin=inputs.angle_table(m))
+    a = oracle.siddon_csr(g)
+    at = oracle.transpose(a)
+    rng = np.random.default_rng(11)
+    x = rng.uniform(0, 1, size=(S, n * n))
+    y = rng.uniform(0, 1, size=(S, m * nd))
+    with xct.Plan(n, m, nd, "f16", cos_sin=g.table(), paired_rows=True, autotune=True) as p:
+        st = p.stats()
+        yo = p.project(torch.tensor(x.reshape(S, n, n), dtype=torch.float32, device="cuda"))
+        xo = p.backproject(torch.tensor(y.reshape(S, m, nd), dtype=torch.float32, device="cuda"))
+        torch.cuda.synchronize()
+    assert st["slots_a_paired"] > 0 and st["slots_at_paired"] > 0
+    x32 = x.astype(np.float32).astype(np.float64)
+    y32 = y.astype(np.float32).astype(np.float64)
+    for got, mat, v in ((yo, a, x32), (xo, at, y32)):
+        absm = oracle.CSR(mat.nrow, mat.ncol, mat.rowptr, mat.col, np.abs(mat.val))
+        _check(got.cpu().numpy().reshape(S, -1), oracle.mixed_project(mat, v, "f16"),
+               oracle.project(absm, np.abs(v)))
