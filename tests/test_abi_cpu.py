@@ -89,3 +89,35 @@ def test_allocator_callbacks_must_pair(lib):
     r = lib.xct_set_allocator(xct.ALLOC_FN(lambda *a: None), xct.FREE_FN(), None)
     assert r == xct.XCT_ERR_INVALID
     xct.xct_set_allocator(None, None)
+
+
+def test_binding_constants_match_the_header():
+    """Every `#define XCT_...` value of include/xct.h has the same value in
+    the Python binding (flags, export selectors, CGLS flags)."""
+    with open(os.path.join(ROOT, "include", "xct.h")) as f:
+        text = f.read()
+    defines = dict(re.findall(r"#define\s+(XCT_[A-Z0-9_]+)\s+(\d+)u?\b", text))
+    assert {"XCT_PLAN_PAIRED_ROWS", "XCT_EXPORT_A_PAIRED", "XCT_EXPORT_AT_PAIRED"} <= set(defines)
+    for name, value in defines.items():
+        assert hasattr(xct, name), name
+        assert getattr(xct, name) == int(value), (name, getattr(xct, name), value)
+
+
+def test_stats_struct_matches_the_header():
+    """The binding's xct_stats mirrors the C struct field by field."""
+    with open(os.path.join(ROOT, "include", "xct.h")) as f:
+        text = f.read()
+    end = text.index("} xct_stats;")
+    body = text[text.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        ctype, names = decl.split(None, 1)
+        for nm in names.split(","):
+            fields.append((nm.strip(), ctype))
+    size = {"int64_t": 8, "int32_t": 4, "double": 8}
+    bound = [(nm, ctypes.sizeof(t)) for nm, t in xct.xct_stats._fields_]
+    assert [(nm, size[t]) for nm, t in fields] == bound
