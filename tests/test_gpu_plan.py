@@ -82,6 +82,24 @@ def test_packed_values_are_rounded_matrix(xct, storage, n, m, nd, off, sp, tile)
             assert np.array_equal(val, rnd(ref.val))
 
 
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("n,m,nd,off,sp,tile", GEOMS)
+def test_paired_layout_is_rounded_matrix(xct, storage, n, m, nd, off, sp, tile):
+    """The paired layouts (XCT_PLAN_PAIRED_ROWS) decoded back: the same
+    matrix, every entry once (a shared slot gives one entry to each row of
+    its pair), values the oracle's rounding, on every plan geometry
+    (ragged Hilbert tiles, rays that miss the grid, a 1-pixel grid)."""
+    g, a, at = _oracle(n, m, nd, off, sp)
+    rnd = {"f16": lambda v: oracle.round_f16(v * 2.0 ** 15) * 2.0 ** -15, "bf16": oracle.round_bf16}[storage]
+    with xct.Plan(n, m, nd, storage, cos_sin=g.table(), det_offset=off, det_spacing=sp,
+                  hilbert_tile=tile, paired_rows=True) as p:
+        for what, ref in ((xct.XCT_EXPORT_A_PAIRED, a), (xct.XCT_EXPORT_AT_PAIRED, at)):
+            rp, col, val = xct.xct_plan_export(p.handle, what)
+            assert np.array_equal(rp, ref.rowptr)
+            assert np.array_equal(col, ref.col)
+            assert np.array_equal(val, rnd(ref.val))
+
+
 def test_default_angle_table_matches_host_library(xct):
     n, m = 16, 37
     g = oracle.Geometry(n=n, m=m, nd=n)          # oracle default: cos/sin(k*pi/m)
