@@ -29,9 +29,12 @@ def _data():
     return x, y
 
 
-def test_wait_limit_zero_times_out_and_recovers(xct):
+@pytest.mark.parametrize("paired", [False, True])
+def test_wait_limit_zero_times_out_and_recovers(xct, paired):
+    """On the plain layouts and on paired ones (the same waits in the
+    paired kernel)."""
     x, y = _data()
-    with xct.Plan(N, M, ND, "f16", cos_sin=inputs.angle_table(M)) as p:
+    with xct.Plan(N, M, ND, "f16", cos_sin=inputs.angle_table(M), paired_rows=paired) as p:
         ref = p.project(x).clone()
         torch.cuda.synchronize()
         xct.xct_plan_check(p.handle)
