@@ -98,8 +98,8 @@ class _Budget:
         torch.cuda.caching_allocator_delete(ptr)
 
 
-def _plan_and_solve(xct, geom, y):
-    h = xct.xct_plan(geom, "f16")
+def _plan_and_solve(xct, geom, y, flags=0):
+    h = xct.xct_plan(geom, "f16", flags)
     try:
         xo = torch.empty((S, N, N), device="cuda")
         xct.xct_cgls(h, y, xo, S, 3)
@@ -108,7 +108,11 @@ def _plan_and_solve(xct, geom, y):
         xct.xct_free(h)
 
 
-def test_allocation_failures_return_oom_without_leaks(xct):
+@pytest.mark.parametrize("paired", [False, True])
+def test_allocation_failures_return_oom_without_leaks(xct, paired):
+    """Also for a plan with paired layouts (their build is the last part of
+    the plan's, so the failure points near the end fall inside it)."""
+    flags = xct.XCT_PLAN_PAIRED_ROWS if paired else 0
     cs = inputs.angle_table(M)
     geom = xct.make_geometry(N, M, ND, cs)
     _, y = _data()
@@ -116,21 +120,21 @@ def test_allocation_failures_return_oom_without_leaks(xct):
     counter = _Budget()
     xct.xct_set_allocator(counter.alloc, counter.release)
     try:
-        h = xct.xct_plan(geom, "f16")
+        h = xct.xct_plan(geom, "f16", flags)
         n_plan = counter.count
         xct.xct_free(h)
-        _plan_and_solve(xct, geom, y)
+        _plan_and_solve(xct, geom, y, flags)
         n_total = counter.count - n_plan
     finally:
         xct.xct_set_allocator(None, None)
     torch.cuda.synchronize()
     assert counter.live == {} and n_total > n_plan > 5
-    for ok in (0, 1, n_plan // 2, n_plan - 1, n_plan + 2, n_total - 1):
+    for ok in (0, 1, n_plan // 2, n_plan - 12, n_plan - 5, n_plan - 1, n_plan + 2, n_total - 1):
         budget = _Budget(ok)
         xct.xct_set_allocator(budget.alloc, budget.release)
         try:
             with pytest.raises(xct.XctError) as ei:
-                _plan_and_solve(xct, geom, y)
+                _plan_and_solve(xct, geom, y, flags)
             assert ei.value.status == xct.XCT_ERR_OOM, (ok, str(ei.value))
             assert "allocator callback failed" in str(ei.value)
         finally:
@@ -138,4 +142,4 @@ def test_allocation_failures_return_oom_without_leaks(xct):
         torch.cuda.synchronize()
         assert budget.live == {}, f"{len(budget.live)} allocations leaked (budget {ok})"
     # the default allocator serves the same calls again
-    _plan_and_solve(xct, geom, y)
+    _plan_and_solve(xct, geom, y, flags)
