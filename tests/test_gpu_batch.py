@@ -36,10 +36,14 @@ def _sinos(key, S, seed):
     return out.astype(np.float32)
 
 
-@pytest.mark.parametrize("kind", ["f16", "f32"])
+@pytest.mark.parametrize("kind", ["f16", "f32", "f16-paired"])
 def test_batch_equals_grouped_solves(xct, kind):
+    """f16-paired: binary16 plans with paired layouts; groups B and C run
+    64-slice tiles on them, in one launch per product phase."""
     iters = 12
-    plans = {k: xct.Plan(n, m, nd, kind, cos_sin=inputs.angle_table(m), det_offset=off)
+    storage, paired = kind.split("-")[0], kind.endswith("-paired")
+    plans = {k: xct.Plan(n, m, nd, storage, cos_sin=inputs.angle_table(m), det_offset=off,
+                         paired_rows=paired)
              for k, (n, m, nd, off) in GEOMS.items()}
     try:
         ys = [torch.tensor(_sinos(k, S, 10 + i), device="cuda") for i, (k, S) in enumerate(JOBS)]
