@@ -1,6 +1,7 @@
 """Parity at the benchmark's full size (512^2 grid, 768 angles, 512 bins,
 64 slices) in the launch configuration the benchmark times (slice tiles of
-64 for 16-bit storage, 32 for FP32).  The oracle computes sampled outputs
+64 for 16-bit storage, 32 for FP32; the benchmark's binary16 solve on paired
+layouts, XCT_PLAN_PAIRED_ROWS).  The oracle computes sampled outputs
 one by one: projections of sampled rays and back projections of sampled
 pixels (matrix-free), and the full FP64 CGLS of two sampled slices."""
 import numpy as np
@@ -38,10 +39,11 @@ def setup():
     return g, x, y, rays, pixels, ref_y, ref_x
 
 
-@pytest.mark.parametrize("kind", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("kind", ["f32", "f16", "bf16", "f16-paired", "bf16-paired"])
 def test_products_sampled(xct, setup, kind):
     g, x, y, rays, pixels, ref_y, ref_x = setup
-    with xct.Plan(N, M, ND, kind, cos_sin=g.table()) as p:
+    kind, paired = kind.split("-")[0], kind.endswith("-paired")
+    with xct.Plan(N, M, ND, kind, cos_sin=g.table(), paired_rows=paired) as p:
         yo = p.project(torch.tensor(x.reshape(S, N, N), device="cuda"))
         xo = p.backproject(torch.tensor(y.reshape(S, M, ND), device="cuda"))
         torch.cuda.synchronize()
@@ -76,8 +78,9 @@ def test_cgls_sampled_slices(xct):
     xo, logo = oracle.cgls(lambda X: oracle.project(a, X), lambda Y: oracle.backproject(at, Y),
                            b[pick], 4)
     bt = torch.tensor(w["sino"], dtype=torch.float32, device="cuda")
-    for kind, tol in (("f32", 2e-5), ("f16", 2e-3)):
-        with xct.Plan(N, M, ND, kind, cos_sin=w["cos_sin"]) as p:
+    for kind, tol in (("f32", 2e-5), ("f16", 2e-3), ("f16-paired", 2e-3)):
+        storage, paired = kind.split("-")[0], kind.endswith("-paired")
+        with xct.Plan(N, M, ND, storage, cos_sin=w["cos_sin"], paired_rows=paired) as p:
             x4 = p.cgls(bt, 4).reshape(S, -1)[pick].double().cpu().numpy()
             xk, log = p.cgls(bt, K, resid=True)
         assert np.linalg.norm(x4 - xo) / np.linalg.norm(xo) <= tol, kind
@@ -86,7 +89,7 @@ def test_cgls_sampled_slices(xct):
         got_r = log.cpu().numpy()[-1, pick, 0]
         # f32: drift of the updated residual; f16: the residual is updated
         # with the 16-bit product, the recomputation uses the FP64 matrix
-        rtol = 1e-3 if kind == "f32" else 1e-2
+        rtol = 1e-3 if storage == "f32" else 1e-2
         assert np.all(np.abs(got_r - true_r) <= rtol * true_r), (kind, got_r, true_r)
 
 
