@@ -123,10 +123,15 @@ typedef struct xct_plan_s* xct_plan_t;
                                      of the staged rows it otherwise would
                                      at 512^2 x 768 angles (0.86 / 0.75 at
                                      1536^2 x 1024, where neighbouring
-                                     angles diverge more); products of other
-                                     tile widths use the plan's own layouts.
-                                     Adds about 1.2x the packed entries of A
-                                     and A^T to the plan (8 bytes a slot) */
+                                     angles diverge more; the 64-slice
+                                     CGLS of 512^2 x 768 x 512 measured 5%
+                                     faster); products of other tile widths
+                                     use the plan's own layouts, and so do
+                                     64-slice tiles if the paired layouts'
+                                     stage buffers do not fit the product
+                                     kernel (they are then not kept).  Adds
+                                     about 1.2x the packed entries of A and
+                                     A^T to the plan (8 bytes a slot) */
 
 /*
  * xct_plan -- build the memoized operator (Sec. II-B memoization; Sec. III-A1
